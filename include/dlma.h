@@ -1,0 +1,225 @@
+/*
+ * dlma.h -- C ABI of the GB300 (sm_103a) distillation low-mode-averaging
+ * library (arXiv:2201.09729, "Implementing noise reduction techniques into
+ * the OpenQ*D package").
+ *
+ * The calls follow the paper's statement of the problem:
+ *   set the gauge field and the Wilson-clover parameters (Sec. 2, Table 1),
+ *   compute the low modes of the spatial Laplacian per timeslice (Eq. 1,
+ *   Sec. 2), apply / invert the Dirac operator on distillation and noise
+ *   sources (Eq. 4 and the text after Eq. 3), project solutions on V(t)
+ *   (Eq. 1, Eq. 3) and contract into C_rest, C_mixed and C_dist (Eqs. 2-3).
+ *
+ * Conventions (all calls):
+ *   Complex numbers are interleaved (re, im) doubles.  Site index
+ *   s = x + L (y + L (z + L t)), so every timeslice is a contiguous block of
+ *   L^3 sites.  Spinors are [site][spin 4][colour 3] complex; links are
+ *   [site][mu 4][row 3][col 3] complex with mu = 0 time and mu = 1, 2, 3 the
+ *   x, y, z directions.  Colour vectors on a timeslice are [L^3][3] complex.
+ *   Dirac matrices are in the chiral basis: gamma_5 = diag(1, 1, -1, -1),
+ *   gamma_0 = -[[0, 1], [1, 0]], gamma_k = [[0, -i sigma_k], [i sigma_k, 0]].
+ *
+ *   Memory: every data pointer is host or device memory as the dlma_mem
+ *   argument says; device pointers must belong to the context's device.  The
+ *   caller owns every array it passes; the library owns the context, its
+ *   copies of the gauge and clover fields, the cached Laplacian modes and all
+ *   work space.  Calls are ordered on the context's stream and synchronous on
+ *   return.  A context is not thread-safe.
+ *
+ *   Errors: every call returns a dlma_status; nothing is thrown across the
+ *   ABI.  dlma_last_error() gives a one-line description of the last failure.
+ *   On DLMA_ERR_NOT_CONVERGED the outputs hold the best iterate and the info
+ *   records its true residual.
+ */
+#ifndef DLMA_H
+#define DLMA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dlma_ctx dlma_ctx;
+
+typedef enum {
+  DLMA_OK = 0,
+  DLMA_ERR_INVALID_ARG = 1,   /* bad size, pointer, precision or state of the input */
+  DLMA_ERR_NOT_CONVERGED = 2, /* iteration cap reached before the tolerance */
+  DLMA_ERR_NONFINITE = 3,     /* NaN / Inf met in the gauge field or in an iterate */
+  DLMA_ERR_SINGULAR = 4,      /* a clover block could not be inverted */
+  DLMA_ERR_OOM = 5,           /* device allocation failed or exceeds the memory cap */
+  DLMA_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  DLMA_ERR_TIMEOUT = 7,       /* host-side wall-clock limit hit while waiting */
+  DLMA_ERR_STATE = 8          /* call made before its prerequisites (gauge, params) */
+} dlma_status;
+
+typedef enum {
+  DLMA_FP64 = 0,   /* double precision, 18-real links */
+  DLMA_FP32 = 1,   /* single precision, 12-real links (third row rebuilt) */
+  DLMA_FP16S = 2   /* half precision spinors with a per-site fp32 scale, 12-real fp16 links */
+} dlma_prec;
+
+typedef enum { DLMA_MEM_HOST = 0, DLMA_MEM_DEVICE = 1 } dlma_mem;
+
+typedef struct {
+  int L;      /* spatial extent (even, >= 2) */
+  int T;      /* temporal extent (even, >= 2) */
+  int bc_t;   /* 0 periodic, 1 antiperiodic quark fields in time */
+} dlma_lattice;
+
+typedef struct {
+  int iters_inner;     /* inner (low-precision) Krylov iterations summed over restarts */
+  int iters_outer;     /* FP64 defect-correction restarts */
+  double true_resid;   /* ||b - D x||_2 / ||b||_2 on the full lattice, recomputed in FP64 */
+  int converged;       /* 1 if true_resid <= tol */
+} dlma_solve_info;
+
+/* ---- context -------------------------------------------------------------
+ * dlma_create: a context for an L^3 x T lattice on CUDA device `device`;
+ * `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Allocates the index / gauge / clover storage for the lattice.
+ * Errors: INVALID_ARG (odd or < 2 extents, device out of range), OOM, CUDA. */
+dlma_status dlma_create(const dlma_lattice* lat, int device, void* cuda_stream, dlma_ctx** out);
+dlma_status dlma_destroy(dlma_ctx* ctx);
+const char* dlma_last_error(const dlma_ctx* ctx);
+/* Cap on the library's own device work space in bytes (0 = no cap); solves
+ * that would exceed it run in smaller batches, or fail with OOM if one
+ * right-hand side does not fit. */
+dlma_status dlma_set_memory_cap(dlma_ctx* ctx, uint64_t bytes);
+
+/* ---- gauge field and parameters ----------------------------------------
+ * dlma_set_gauge: copy the links U_mu(x) (complex [V][4][3][3]) into the
+ * context and derive the even-odd, 12-real (fp32 / fp16) and spatial-link
+ * copies.  Links are expected in SU(3); the 12-real forms rebuild the third
+ * row as the conjugated cross product of the first two.
+ * Errors: INVALID_ARG (null), NONFINITE (a NaN / Inf link), CUDA. */
+dlma_status dlma_set_gauge(dlma_ctx* ctx, const double* links, dlma_mem mem);
+
+/* dlma_set_params: Wilson-clover parameters of the O(a)-improved Wilson
+ * operator named in the abstract and Sec. 2 (m0-normalised form)
+ *   D psi(x) = T(x) psi(x) - 1/2 sum_mu [(1 - g_mu) U_mu(x) psi(x+mu)
+ *                                       + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu)],
+ *   T(x) = (4 + m0) + c_sw (i/4) sum_{mu,nu} sigma_{mu nu} Fhat_{mu nu}(x),
+ * Fhat = (Q_{mu nu} - Q_{nu mu}) / 8 from the four plaquette leaves; m0 =
+ * 1/(2 kappa) - 4.  Builds the clover field and the inverse of its odd-site
+ * blocks (2 hermitian 6x6 chirality blocks per site).
+ * Errors: STATE (no gauge field), SINGULAR (a block not invertible), CUDA. */
+dlma_status dlma_set_params(dlma_ctx* ctx, double m0, double c_sw);
+
+/* ---- Dirac operator -------------------------------------------------------
+ * dlma_apply_Dw: out = D in for nrhs full-lattice spinor fields
+ * (complex [nrhs][V][4][3]), computed in precision `prec` (inputs and
+ * outputs are always complex128; FP32 / FP16S round the fields on entry).
+ * Errors: STATE, INVALID_ARG, OOM, CUDA. */
+dlma_status dlma_apply_Dw(dlma_ctx* ctx, const double* in, double* out, int nrhs,
+                          dlma_prec prec, dlma_mem mem);
+
+/* dlma_apply_schur: the even-odd Schur operator on even-site fields
+ * (complex [nrhs][V/2][4][3], even sites in lexicographic order):
+ *   dagger = 0: out = Dhat in,  Dhat = T_ee - D_eo T_oo^-1 D_oe
+ *   dagger = 1: out = Dhat^dag in = gamma_5 Dhat gamma_5 in.
+ * Errors: STATE, INVALID_ARG, OOM, CUDA. */
+dlma_status dlma_apply_schur(dlma_ctx* ctx, const double* in, double* out, int nrhs, int dagger,
+                             dlma_prec prec, dlma_mem mem);
+
+/* dlma_solve: x = D^-1 b for nrhs full-lattice sources (complex
+ * [nrhs][V][4][3]); the propagator solves of Eq. 4 and of the perambulator
+ * (text after Eq. 3).  Even-odd Schur system, multi-RHS CG on the normal
+ * equations; `inner` = DLMA_FP64 runs it in double precision, DLMA_FP32 /
+ * DLMA_FP16S run the Krylov bulk in that precision inside FP64 defect
+ * correction.  Each right-hand side stops when its FP64 true residual
+ * ||b - D x|| / ||b|| <= tol and is retired from the batch.  `info` (may be
+ * NULL) receives nrhs records.  A zero source gives x = 0.
+ * Errors: STATE, INVALID_ARG (tol <= 0, nrhs < 1), NOT_CONVERGED, NONFINITE,
+ * OOM, CUDA. */
+dlma_status dlma_solve(dlma_ctx* ctx, const double* b, double* x, int nrhs, double tol,
+                       dlma_prec inner, dlma_solve_info* info, dlma_mem mem);
+
+/* ---- spatial Laplacian (Eq. 1) --------------------------------------------
+ * dlma_apply_laplacian: out = lap(t) in on every timeslice at once for nvec
+ * colour fields over the whole lattice (complex [nvec][V][3]):
+ *   (lap v)(m, t) = -6 v + sum_j [U_j(m,t) v(m+j) + U_j(m-j,t)^dag v(m-j)].
+ * Errors: STATE, INVALID_ARG, CUDA. */
+dlma_status dlma_apply_laplacian(dlma_ctx* ctx, const double* in, double* out, int nvec, dlma_mem mem);
+
+/* dlma_laplacian_eigs: the N lowest eigenpairs of -lap(t) (Eq. 1; "low-lying
+ * modes", Sec. 2), for one timeslice t or for all timeslices at once
+ * (t = -1).  Eigenvalues (of -lap, ascending, in [0, 12]) go to evals
+ * ([N], or [T][N] for t = -1; always HOST memory); eigenvectors, normalised,
+ * go to evecs (complex [N][L^3][3], or [T][N][L^3][3]) in `mem`; evecs may be
+ * NULL.  The modes of every computed timeslice are also cached in the
+ * context.  Each pair meets ||lap v - lam v|| <= tol * max(|lam|, 1).
+ * Errors: STATE, INVALID_ARG (N < 1 or N > 3 L^3 / 2), NOT_CONVERGED, CUDA. */
+dlma_status dlma_laplacian_eigs(dlma_ctx* ctx, int t, int N, double tol, double* evals,
+                                double* evecs, dlma_mem mem);
+
+/* ---- distillation sources, projections, contractions ------------------------
+ * dlma_make_sources: the 4N + 5 n_noise sources of one source timeslice
+ * t_src (complex [4N + 5 n_noise][V][4][3], zero off t_src), from the
+ * modes V (complex [N][L^3][3] of t_src) and the noise eta (complex
+ * [n_noise][L^3][4][3]):
+ *   source 4k + alpha            = v_k (x) e_alpha                 (perambulator)
+ *   source 4N + 5r + 0           = eta_r                           (Eq. 4, phi)
+ *   source 4N + 5r + 1           = (1 - Box(t')) eta_r             (Eq. 4, phibar)
+ *   source 4N + 5r + 1 + k       = gamma_5 gamma_k (1 - Box(t')) eta_r, k = 1..3
+ * (the last three give the vector-channel left vectors of the one-end
+ * estimator with an undiluted noise).  Errors: INVALID_ARG, CUDA. */
+dlma_status dlma_make_sources(dlma_ctx* ctx, int t_src, int N, const double* V, int n_noise,
+                              const double* eta, double* b, dlma_mem mem);
+
+/* dlma_project: coefficients c = V(t)^dag psi(t) per spin (Eq. 1, Eq. 3),
+ * for one timeslice t or every timeslice (t = -1):
+ *   coeff[j][t][alpha][k] = sum_{m, c} conj(V_t[k][m][c]) psi_j(m, t, alpha, c)
+ * V is complex [N][L^3][3] (t >= 0) or [T][N][L^3][3] (t = -1); psi complex
+ * [nrhs][V][4][3]; coeff complex [nrhs][T or 1][4][N].
+ * Errors: INVALID_ARG, CUDA. */
+dlma_status dlma_project(dlma_ctx* ctx, int t, const double* V, int N, const double* psi, int nrhs,
+                         double* coeff, dlma_mem mem);
+
+/* dlma_contract: the correlator parts of Eqs. 2-3 for one source timeslice,
+ * from the solutions of dlma_make_sources' sources (phi complex
+ * [4N + 5 n_noise][V][4][3], in that order) and the modes of every timeslice
+ * (V complex [T][N][L^3][3]).  For the four channels G in (gamma_5, gamma_1,
+ * gamma_2, gamma_3), with sink and source Gamma equal:
+ *   C_dist(t)  = tr[g5 G tau(t) G g5 tau(t)^dag],  tau = V(t)^dag D^-1 V(t')
+ *   C_mixed(t) = 1/N_r sum_r sum_{x in t} chi_r^dag g5 G Box(t) phi_r
+ *   C_rest(t)  = 1/N_r sum_r sum_{x in t} chi_r^dag g5 G (1 - Box(t)) phi_r
+ * chi_r = phibar_r (G = g5) or the gamma_5 gamma_k solution (G = g_k).
+ * Outputs are complex [4][T] (channel-major), always HOST memory.
+ * Errors: INVALID_ARG, CUDA. */
+dlma_status dlma_contract(dlma_ctx* ctx, int t_src, int N, const double* V, int n_noise,
+                          const double* phi, double* C_dist, double* C_rest, double* C_mixed,
+                          dlma_mem mem);
+
+/* dlma_correlators: the whole per-source-timeslice pipeline on the device --
+ * sources, solves (precision `inner`, tolerance tol, in batches that fit the
+ * memory cap), projections and contractions -- using the modes cached by
+ * dlma_laplacian_eigs(t = -1, N).  eta complex [n_noise][L^3][4][3] in
+ * `mem`; outputs complex [4][T] HOST; info (may be NULL) gets 4N + 5 n_noise
+ * records.  Errors: STATE (no cached modes for N), plus those of dlma_solve. */
+dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* eta,
+                             double tol, dlma_prec inner, double* C_dist, double* C_rest,
+                             double* C_mixed, dlma_solve_info* info, dlma_mem mem);
+
+/* ---- introspection ---------------------------------------------------------
+ * dlma_index_tables: the device's even-odd index arithmetic written out:
+ * eo_index[V] (compressed index of every site within its parity) and
+ * nbr[2][8][V/2] (for output parity p, direction d = 2 mu + (0 fwd, 1 bwd),
+ * the compressed index of the neighbour in parity 1 - p).  HOST memory.
+ * Errors: INVALID_ARG, CUDA. */
+dlma_status dlma_index_tables(dlma_ctx* ctx, int32_t* eo_index, int32_t* nbr);
+
+/* dlma_kernel_launches: number of kernels the library launched on this
+ * context since creation (graph-replayed kernels included). */
+uint64_t dlma_kernel_launches(const dlma_ctx* ctx);
+
+/* dlma_last_timing_ms: device time (CUDA events on the context's stream) of
+ * named phases of the last call: index 0 the whole call, 1 the dominant
+ * stencil kernel summed, 2 the number of dominant-kernel launches. */
+dlma_status dlma_last_timing(const dlma_ctx* ctx, double* out3);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DLMA_H */

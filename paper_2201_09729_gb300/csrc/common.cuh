@@ -1,0 +1,232 @@
+// Shared device / host helpers of the dlma library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdarg.h>
+#include <string.h>
+#include <vector>
+#include <string>
+
+#include "../../include/dlma.h"
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on (re, im) pairs, templated on the real type
+template <class R> struct Cx { R re, im; };
+
+template <class R> __host__ __device__ __forceinline__ Cx<R> cx(R a, R b) { Cx<R> z; z.re = a; z.im = b; return z; }
+template <class R> __host__ __device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) { return cx<R>(a.re + b.re, a.im + b.im); }
+template <class R> __host__ __device__ __forceinline__ Cx<R> operator-(Cx<R> a, Cx<R> b) { return cx<R>(a.re - b.re, a.im - b.im); }
+template <class R> __host__ __device__ __forceinline__ Cx<R> operator-(Cx<R> a) { return cx<R>(-a.re, -a.im); }
+template <class R> __host__ __device__ __forceinline__ Cx<R> operator*(Cx<R> a, Cx<R> b) {
+  return cx<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class R> __host__ __device__ __forceinline__ Cx<R> operator*(R s, Cx<R> a) { return cx<R>(s * a.re, s * a.im); }
+template <class R> __host__ __device__ __forceinline__ Cx<R> conj(Cx<R> a) { return cx<R>(a.re, -a.im); }
+// i * a
+template <class R> __host__ __device__ __forceinline__ Cx<R> mul_i(Cx<R> a) { return cx<R>(-a.im, a.re); }
+// a += b * c
+template <class R> __host__ __device__ __forceinline__ void fma_acc(Cx<R>& a, Cx<R> b, Cx<R> c) {
+  a.re = fma(b.re, c.re, a.re); a.re = fma(-b.im, c.im, a.re);
+  a.im = fma(b.re, c.im, a.im); a.im = fma(b.im, c.re, a.im);
+}
+// a += conj(b) * c
+template <class R> __host__ __device__ __forceinline__ void fma_conj_acc(Cx<R>& a, Cx<R> b, Cx<R> c) {
+  a.re = fma(b.re, c.re, a.re); a.re = fma(b.im, c.im, a.re);
+  a.im = fma(b.re, c.im, a.im); a.im = fma(-b.im, c.re, a.im);
+}
+template <class R> __host__ __device__ __forceinline__ R norm2(Cx<R> a) { return a.re * a.re + a.im * a.im; }
+
+// ---------------------------------------------------------------------------
+// lattice geometry: even-odd compressed index <-> coordinates.
+// Site s = x + L (y + L (z + L t)); parity p = (x+y+z+t) & 1; for even L the
+// compressed index of s within its parity is s >> 1.
+struct Geom {
+  int L, T, V, Vh, Vs;
+};
+
+struct Coord { int x, y, z, t; };
+
+__host__ __device__ __forceinline__ Coord eo_coords(const Geom& g, int p, int i) {
+  int s0 = 2 * i;
+  Coord c;
+  int x0 = s0 % g.L;
+  int r = s0 / g.L;
+  c.y = r % g.L; r /= g.L;
+  c.z = r % g.L;
+  c.t = r / g.L;
+  c.x = x0 + ((c.y + c.z + c.t + p) & 1);
+  return c;
+}
+__host__ __device__ __forceinline__ int lex_of(const Geom& g, int x, int y, int z, int t) {
+  return x + g.L * (y + g.L * (z + g.L * t));
+}
+// neighbour in direction mu (0 t, 1 x, 2 y, 3 z), sign +1 / -1, periodic wrap; lexicographic index
+__host__ __device__ __forceinline__ int nbr_lex(const Geom& g, Coord c, int mu, int sgn) {
+  int x = c.x, y = c.y, z = c.z, t = c.t;
+  if (mu == 0) { t += sgn; t = t < 0 ? g.T - 1 : (t >= g.T ? 0 : t); }
+  else if (mu == 1) { x += sgn; x = x < 0 ? g.L - 1 : (x >= g.L ? 0 : x); }
+  else if (mu == 2) { y += sgn; y = y < 0 ? g.L - 1 : (y >= g.L ? 0 : y); }
+  else { z += sgn; z = z < 0 ? g.L - 1 : (z >= g.L ? 0 : z); }
+  return lex_of(g, x, y, z, t);
+}
+
+// ---------------------------------------------------------------------------
+// device buffers owned by the context (grow-on-demand work space)
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct dlma_ctx {
+  Geom g;
+  int bc_t = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;      // created by dlma_create when the caller passed NULL
+  char err[512];
+  uint64_t launches = 0;
+  uint64_t memcap = 0;
+  uint64_t work_bytes = 0;      // bytes currently held in work buffers
+  double timing[3] = {0, 0, 0};
+
+  bool have_gauge = false, have_params = false;
+  double m0 = 0, csw = 0;
+
+  // gauge: U_mu(x) for x in parity p, SoA over the compressed site index
+  double2* Ucan = nullptr;  // [V][4][3][3] canonical copy (clover build)
+  double2* U64 = nullptr;   // [2][4][9][Vh]
+  float4* U32 = nullptr;    // [2][4][3][Vh]  rows 0, 1 (12 reals)
+  uint4* U16a = nullptr;    // [2][4][Vh]     halves 0..7 of rows 0, 1
+  uint2* U16b = nullptr;    // [2][4][Vh]     halves 8..11
+  double2* U3 = nullptr;    // [3][9][V]      spatial links, lexicographic, for the Laplacian
+  float4* U3f = nullptr;    // [3][3][V]      spatial links 12-real fp32
+  // clover: 2 hermitian 6x6 blocks per site packed as 72 reals
+  // (per block: 6 real diagonal entries, then the 15 complex entries below the diagonal, row-major)
+  double2* C64 = nullptr;   // [2][36][Vh]  T(x)
+  double2* Ci64 = nullptr;  // [2][36][Vh]  T(x)^-1
+  float4* C32 = nullptr;    // [2][18][Vh]
+  float4* Ci32 = nullptr;
+  uint4* C16 = nullptr;     // [2][9][Vh]
+  uint4* Ci16 = nullptr;
+  int* flag = nullptr;      // device status flags [16]
+
+  // cached Laplacian modes (all timeslices)
+  int eig_N = 0;
+  double2* eig_V = nullptr;       // [N][T][Vs][3]
+  std::vector<double> eig_lam;    // [T][N]
+
+  // named work buffers
+  DevBuf wb[64];
+  void* pinned = nullptr;         // small pinned host staging area
+};
+
+enum WorkSlot {
+  WS_IN = 0, WS_OUT, WS_T0, WS_T1, WS_T2,
+  WS_SOLVE_B, WS_SOLVE_X64, WS_SOLVE_R64, WS_SOLVE_BH, WS_SOLVE_TMP64,
+  WS_CG_X, WS_CG_R, WS_CG_P, WS_CG_PLO, WS_CG_Q, WS_CG_Z, WS_CG_TMP, WS_CG_RHS,
+  WS_SCAL, WS_PART, WS_ACT, WS_ITERS,
+  WS_EIG_X, WS_EIG_Y, WS_EIG_Y2, WS_EIG_W, WS_EIG_G, WS_EIG_PART, WS_EIG_S, WS_EIG_AUX,
+  WS_PROJ_V, WS_PROJ_PART, WS_PROJ_C, WS_CON, WS_CON2, WS_SRC, WS_SOL, WS_ETA,
+  WS_COUNT
+};
+
+// ---------------------------------------------------------------------------
+// error handling
+dlma_status set_err(dlma_ctx* ctx, dlma_status st, const char* fmt, ...);
+
+#define CU(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return set_err(ctx, DLMA_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, \
+                     cudaGetErrorString(e_));                                      \
+  } while (0)
+
+#define CHECK_LAUNCH()                                                              \
+  do {                                                                              \
+    cudaError_t e_ = cudaGetLastError();                                            \
+    if (e_ != cudaSuccess)                                                          \
+      return set_err(ctx, DLMA_ERR_CUDA, "%s:%d launch: %s", __FILE__, __LINE__,      \
+                     cudaGetErrorString(e_));                                       \
+    ctx->launches++;                                                                \
+  } while (0)
+
+#define TRY(call)                       \
+  do {                                  \
+    dlma_status s_ = (call);            \
+    if (s_ != DLMA_OK) return s_;       \
+  } while (0)
+
+// work buffer of at least `bytes` in slot `slot` (contents not preserved on growth)
+dlma_status work(dlma_ctx* ctx, int slot, size_t bytes, void** out);
+template <class T> dlma_status workT(dlma_ctx* ctx, int slot, size_t count, T** out) {
+  void* p;
+  dlma_status s = work(ctx, slot, count * sizeof(T), &p);
+  *out = (T*)p;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// internal fields: even-odd half-lattice spinors in one precision, SoA over
+// the compressed site index.  Per right-hand side:
+//   FP64  double2 [12][Vh]
+//   FP32  float4  [6][Vh]      (complex components 2q, 2q+1 in one float4)
+//   FP16S uint4   [3][Vh]      (complex components 4q..4q+3) + float scale [Vh]
+struct Field {
+  void* data = nullptr;
+  float* scale = nullptr;
+  int prec = DLMA_FP64;
+  int nrhs = 0;
+  int Vh = 0;
+};
+
+__host__ __device__ inline size_t field_units_per_rhs(int prec, int Vh) {
+  return prec == DLMA_FP64 ? (size_t)12 * Vh : prec == DLMA_FP32 ? (size_t)6 * Vh : (size_t)3 * Vh;
+}
+inline size_t field_bytes_per_rhs(int prec, int Vh) {
+  return prec == DLMA_FP64 ? (size_t)12 * Vh * 16 : prec == DLMA_FP32 ? (size_t)6 * Vh * 16
+                                                                      : (size_t)3 * Vh * 16 + (size_t)Vh * 4;
+}
+dlma_status field_alloc(dlma_ctx* ctx, int slot, int prec, int nrhs, Field* f);
+
+// ---------------------------------------------------------------------------
+// cross-file internal entry points
+dlma_status copy_in(dlma_ctx* ctx, int slot, const double* p, size_t bytes, dlma_mem mem, const double** dev);
+dlma_status copy_out(dlma_ctx* ctx, double* dst, const double* dev, size_t bytes, dlma_mem mem);
+
+// pack canonical complex128 [nrhs][V][4][3] (full lattice) parity p -> field
+dlma_status pack_parity(dlma_ctx* ctx, const double* src, int full, int p, Field& f);
+// unpack field parity p -> canonical complex128 (full lattice or half)
+dlma_status unpack_parity(dlma_ctx* ctx, const Field& f, int full, int p, double* dst);
+
+// stencil (hop) launch: out_p = Kout * (Kown * own + s * hop(in_{1-p}))
+struct HopOp {
+  int p_out;          // parity of the output sites
+  int g5_in = 0;      // apply gamma_5 to the hopping input
+  int g5_hop = 0;     // apply gamma_5 to the hopping result
+  int own = 0;        // 0: no own-site term, 1: identity, 2: clover T_p, 3: clover inverse T_p^-1
+  int kout = 0;       // 0: none, 2: T_p, 3: T_p^-1 applied to the sum
+  int hop = 1;        // include the hopping term
+  double s = 1.0;     // sign / factor of the hopping term
+  double* norm_part = nullptr;   // if set: per (rhs, block) partial |out|^2
+  const int* active = nullptr;   // per-rhs mask (nullptr = all)
+};
+dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Field* own, Field& out,
+                       int* nblocks_out = nullptr);
+int hop_grid_x(dlma_ctx* ctx, int prec);
+
+// Schur operator on even fields: out = Dhat in (dagger: gamma5 Dhat gamma5), tmp: odd work field
+dlma_status schur_apply(dlma_ctx* ctx, const Field& in, Field& tmp, Field& out, int dagger,
+                        const int* active, double* norm_part);
+
+dlma_status eig_run(dlma_ctx* ctx, int N, double tol);
+dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol,
+                         dlma_prec inner, dlma_solve_info* info);
+
+// per-context event timer helper
+struct EvTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+};

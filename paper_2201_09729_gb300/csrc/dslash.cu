@@ -1,0 +1,540 @@
+// Even-odd Wilson-clover stencil (the Dirac operator of the abstract / Sec. 2,
+// m0-normalised O(a)-improved Wilson quarks):
+//
+//   hop(psi)(x) = -1/2 sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ]
+//   out_p = Kout * ( Kown * own_p + s * hop(in_{1-p}) )
+//
+// with Kown / Kout one of {1, T_p, T_p^-1}; this single kernel family gives
+// the full operator, the Schur complement Dhat = T_ee - D_eo T_oo^-1 D_oe, its
+// gamma_5 adjoint and the even-odd source preparation / solution
+// reconstruction.  One thread per (output site, right-hand side); a block is
+// SX sites x SY right-hand sides, so the SY warps of a site tile share the
+// link and clover loads through L1.  Spin projection uses the chiral basis
+// (gamma_5 = diag(1,1,-1,-1)): every (1 -+ g_mu) halves the colour work.
+#include "common.cuh"
+
+#include "fieldio.cuh"
+
+// link U_mu(x) for x of parity p at compressed index i
+template <int P>
+__device__ __forceinline__ void load_link(const void* __restrict__ Ua, const void* __restrict__ Ub, int p, int mu,
+                                          int i, int Vh, Cx<typename PT<P>::R> U[3][3]) {
+  typedef typename PT<P>::R R;
+  size_t base = (size_t)(p * 4 + mu);
+  if (P == DLMA_FP64) {
+    const double2* u = (const double2*)Ua;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      double2 v = __ldg(u + (base * 9 + k) * Vh + i);
+      U[k / 3][k % 3] = cx<R>((R)v.x, (R)v.y);
+    }
+    return;
+  }
+  if (P == DLMA_FP32) {
+    const float4* u = (const float4*)Ua;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      float4 v = __ldg(u + (base * 3 + q) * Vh + i);
+      U[(2 * q) / 3][(2 * q) % 3] = cx<R>(v.x, v.y);
+      U[(2 * q + 1) / 3][(2 * q + 1) % 3] = cx<R>(v.z, v.w);
+    }
+  } else {
+    uint4 a = __ldg((const uint4*)Ua + base * Vh + i);
+    uint2 b = __ldg((const uint2*)Ub + base * Vh + i);
+    unsigned w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      float2 f = __half22float2(*(__half2*)&w[k]);
+      U[k / 3][k % 3] = cx<R>(f.x, f.y);
+    }
+  }
+  // third row = conj(row0 x row1)  (SU(3) reconstruction from 12 reals)
+  U[2][0] = conj(U[0][1] * U[1][2] - U[0][2] * U[1][1]);
+  U[2][1] = conj(U[0][2] * U[1][0] - U[0][0] * U[1][2]);
+  U[2][2] = conj(U[0][0] * U[1][1] - U[0][1] * U[1][0]);
+}
+
+// one chirality block (36 packed reals) of a clover-type field at parity-offset base
+template <int P>
+__device__ __forceinline__ void load_clover_block(const void* __restrict__ C, int i, int Vh, int ch,
+                                                  typename PT<P>::R a[36]) {
+  typedef typename PT<P>::R R;
+  if (P == DLMA_FP64) {
+    const double2* c = (const double2*)C;
+#pragma unroll
+    for (int q = 0; q < 18; q++) {
+      double2 v = __ldg(c + (size_t)(18 * ch + q) * Vh + i);
+      a[2 * q] = (R)v.x;
+      a[2 * q + 1] = (R)v.y;
+    }
+  } else if (P == DLMA_FP32) {
+    const float4* c = (const float4*)C;
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+      float4 v = __ldg(c + (size_t)(9 * ch + q) * Vh + i);
+      a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
+    }
+  } else {
+    const uint4* c = (const uint4*)C;
+    // block ch occupies halves [36 ch, 36 ch + 36) of 72: uint4 words 4 ch .. 4 ch + 4
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+      uint4 v = __ldg(c + (size_t)(4 * ch + q) * Vh + i);
+      unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        float2 f = __half22float2(*(__half2*)&w[r]);
+        int h = 8 * q + 2 * r - 4 * ch;   // index of f.x within this block
+        if (h >= 0 && h < 36) a[h] = f.x;
+        if (h + 1 >= 0 && h + 1 < 36) a[h + 1] = f.y;
+      }
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void clover_apply(const void* __restrict__ C, int i, int Vh,
+                                             Spinor<typename PT<P>::R>& v) {
+  typedef typename PT<P>::R R;
+#pragma unroll
+  for (int ch = 0; ch < 2; ch++) {
+    R a[36];
+    load_clover_block<P>(C, i, Vh, ch, a);
+    Cx<R> in[6], out[6];
+#pragma unroll
+    for (int r = 0; r < 6; r++) {
+      in[r] = v.c[2 * ch + r / 3][r % 3];
+      out[r] = a[r] * in[r];
+    }
+    int k = 6;
+#pragma unroll
+    for (int r = 1; r < 6; r++)
+#pragma unroll
+      for (int c = 0; c < r; c++) {
+        Cx<R> l = cx<R>(a[k], a[k + 1]);
+        k += 2;
+        fma_acc(out[r], l, in[c]);
+        fma_conj_acc(out[c], l, in[r]);
+      }
+#pragma unroll
+    for (int r = 0; r < 6; r++) v.c[2 * ch + r / 3][r % 3] = out[r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct HopArgs {
+  Geom g;
+  int bc_t, p_out, nrhs;
+  const void* in; const float* in_scale; size_t in_stride;
+  const void* own; const float* own_scale; size_t own_stride;
+  void* out; float* out_scale; size_t out_stride;
+  const void* Ua; const void* Ub;
+  const void* Kown; const void* Kout;   // already offset to parity p_out
+  double s;
+  double* norm_part;
+  const int* active;
+};
+
+template <class R>
+__device__ __forceinline__ void su3_mul(const Cx<R> U[3][3], const Cx<R> h[3], Cx<R> w[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    Cx<R> s = U[a][0] * h[0];
+    fma_acc(s, U[a][1], h[1]);
+    fma_acc(s, U[a][2], h[2]);
+    w[a] = s;
+  }
+}
+template <class R>
+__device__ __forceinline__ void su3_dag_mul(const Cx<R> U[3][3], const Cx<R> h[3], Cx<R> w[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    Cx<R> s = cx<R>(0, 0);
+    fma_conj_acc(s, U[0][a], h[0]);
+    fma_conj_acc(s, U[1][a], h[1]);
+    fma_conj_acc(s, U[2][a], h[2]);
+    w[a] = s;
+  }
+}
+
+template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM>
+__global__ void __launch_bounds__(256) k_hop(HopArgs a) {
+  typedef typename PT<P>::R R;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const Geom g = a.g;
+  bool valid = i < g.Vh && j < a.nrhs;
+  if (valid && a.active) valid = a.active[j] != 0;
+  double nrm = 0.0;
+  if (valid) {
+    Spinor<R> res;
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) res.c[s][c] = cx<R>(0, 0);
+    if (HOP) {
+      const Coord co = eo_coords(g, a.p_out, i);
+      const char* inb = (const char*)a.in;
+      const void* in_j = inb + (size_t)j * a.in_stride;
+      const float* sc_j = a.in_scale ? a.in_scale + (size_t)j * g.Vh : nullptr;
+#pragma unroll
+      for (int mu = 0; mu < 4; mu++) {
+#pragma unroll
+        for (int dir = 0; dir < 2; dir++) {
+          const int sgn = dir == 0 ? +1 : -1;
+          const int n = nbr_lex(g, co, mu, sgn) >> 1;
+          Spinor<R> ps = load_spinor<P>(in_j, sc_j, g.Vh, n);
+          if (G5IN) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) { ps.c[2][c] = -ps.c[2][c]; ps.c[3][c] = -ps.c[3][c]; }
+          }
+          Cx<R> U[3][3];
+          // forward: U_mu(x) at this site; backward: U_mu(x - mu) at the neighbour
+          load_link<P>(a.Ua, a.Ub, dir == 0 ? a.p_out : 1 - a.p_out, mu, dir == 0 ? i : n, g.Vh, U);
+          R ph = 1;
+          if (mu == 0 && a.bc_t) {
+            if (dir == 0 && co.t == g.T - 1) ph = -1;
+            if (dir == 1 && co.t == 0) ph = -1;
+          }
+          Cx<R> h0[3], h1[3], w0[3], w1[3];
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const Cx<R> u0 = ps.c[0][c], u1 = ps.c[1][c], d0 = ps.c[2][c], d1 = ps.c[3][c];
+            if (dir == 0) {           // (1 - g_mu)
+              if (mu == 0) { h0[c] = u0 + d0; h1[c] = u1 + d1; }
+              else if (mu == 1) { h0[c] = u0 + mul_i(d1); h1[c] = u1 + mul_i(d0); }
+              else if (mu == 2) { h0[c] = u0 + d1; h1[c] = u1 - d0; }
+              else { h0[c] = u0 + mul_i(d0); h1[c] = u1 - mul_i(d1); }
+            } else {                  // (1 + g_mu)
+              if (mu == 0) { h0[c] = u0 - d0; h1[c] = u1 - d1; }
+              else if (mu == 1) { h0[c] = u0 - mul_i(d1); h1[c] = u1 - mul_i(d0); }
+              else if (mu == 2) { h0[c] = u0 - d1; h1[c] = u1 + d0; }
+              else { h0[c] = u0 - mul_i(d0); h1[c] = u1 + mul_i(d1); }
+            }
+          }
+          if (dir == 0) { su3_mul(U, h0, w0); su3_mul(U, h1, w1); }
+          else { su3_dag_mul(U, h0, w0); su3_dag_mul(U, h1, w1); }
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const Cx<R> x0 = ph * w0[c], x1 = ph * w1[c];
+            res.c[0][c] = res.c[0][c] + x0;
+            res.c[1][c] = res.c[1][c] + x1;
+            if (dir == 0) {
+              if (mu == 0) { res.c[2][c] = res.c[2][c] + x0; res.c[3][c] = res.c[3][c] + x1; }
+              else if (mu == 1) { res.c[2][c] = res.c[2][c] - mul_i(x1); res.c[3][c] = res.c[3][c] - mul_i(x0); }
+              else if (mu == 2) { res.c[2][c] = res.c[2][c] - x1; res.c[3][c] = res.c[3][c] + x0; }
+              else { res.c[2][c] = res.c[2][c] - mul_i(x0); res.c[3][c] = res.c[3][c] + mul_i(x1); }
+            } else {
+              if (mu == 0) { res.c[2][c] = res.c[2][c] - x0; res.c[3][c] = res.c[3][c] - x1; }
+              else if (mu == 1) { res.c[2][c] = res.c[2][c] + mul_i(x1); res.c[3][c] = res.c[3][c] + mul_i(x0); }
+              else if (mu == 2) { res.c[2][c] = res.c[2][c] + x1; res.c[3][c] = res.c[3][c] - x0; }
+              else { res.c[2][c] = res.c[2][c] + mul_i(x0); res.c[3][c] = res.c[3][c] - mul_i(x1); }
+            }
+          }
+        }
+      }
+      const R f = (R)(-0.5 * a.s);
+#pragma unroll
+      for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          R ff = (G5HOP && s >= 2) ? -f : f;
+          res.c[s][c] = ff * res.c[s][c];
+        }
+    }
+    if (OWN) {
+      const void* own_j = (const char*)a.own + (size_t)j * a.own_stride;
+      const float* osc = a.own_scale ? a.own_scale + (size_t)j * g.Vh : nullptr;
+      Spinor<R> o = load_spinor<P>(own_j, osc, g.Vh, i);
+      if (OWN == 2) clover_apply<P>(a.Kown, i, g.Vh, o);
+#pragma unroll
+      for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) res.c[s][c] = res.c[s][c] + o.c[s][c];
+    }
+    if (KOUT) clover_apply<P>(a.Kout, i, g.Vh, res);
+    store_spinor<P>((char*)a.out + (size_t)j * a.out_stride, a.out_scale ? a.out_scale + (size_t)j * g.Vh : nullptr,
+                    g.Vh, i, res);
+    if (NORM) {
+#pragma unroll
+      for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) nrm += (double)norm2(res.c[s][c]);
+    }
+  }
+  if (NORM) {
+    // per (rhs, block) partial sum: warps run along x for one rhs row
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    const int wx = threadIdx.x >> 5, nwx = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.y * nwx + wx] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0 && j < a.nrhs) {
+      double t = 0;
+      for (int w = 0; w < nwx; w++) t += red[threadIdx.y * nwx + w];
+      a.norm_part[(size_t)j * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host dispatch
+static inline void hop_block(int prec, int& sx, int& sy) {
+  (void)prec;
+  sx = 64;
+  sy = 4;
+}
+
+int hop_grid_x(dlma_ctx* ctx, int prec) {
+  int sx, sy;
+  hop_block(prec, sx, sy);
+  return (ctx->g.Vh + sx - 1) / sx;
+}
+
+template <int P>
+static void dispatch(const HopOp& op, dim3 grid, dim3 blk, cudaStream_t st, const HopArgs& a) {
+  const bool norm = op.norm_part != nullptr;
+#define L(G5I, G5H, OWN, KO, HOP, NRM) k_hop<P, G5I, G5H, OWN, KO, HOP, NRM><<<grid, blk, 0, st>>>(a)
+  if (!op.hop) {                                   // Kout * (Kown * own)
+    if (op.own == 1 && op.kout) L(false, false, 1, true, false, false);
+    else if (op.own == 2 && !op.kout) L(false, false, 2, false, false, false);
+    else L(false, false, 1, false, false, false);
+    return;
+  }
+  if (op.own == 0 && op.kout) {                    // Schur step A (and its dagger)
+    if (op.g5_in) L(true, false, 0, true, true, false);
+    else L(false, false, 0, true, true, false);
+  } else if (op.own >= 2 && !op.kout) {            // Schur step B / full operator
+    if (op.g5_hop) { if (norm) L(false, true, 2, false, true, true); else L(false, true, 2, false, true, false); }
+    else { if (norm) L(false, false, 2, false, true, true); else L(false, false, 2, false, true, false); }
+  } else if (op.own == 1 && op.kout) {             // reconstruct: T^-1 (b - hop x)
+    L(false, false, 1, true, true, false);
+  } else if (op.own == 1 && !op.kout) {            // prepare: b - hop(tmp)
+    if (norm) L(false, false, 1, false, true, true); else L(false, false, 1, false, true, false);
+  } else {                                         // plain hop
+    L(false, false, 0, false, true, false);
+  }
+#undef L
+}
+
+dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Field* own, Field& out,
+                       int* nblocks_out) {
+  const int P = out.prec;
+  HopArgs a;
+  a.g = ctx->g;
+  a.bc_t = ctx->bc_t;
+  a.p_out = op.p_out;
+  a.nrhs = out.nrhs;
+  a.in = in.data;
+  a.in_scale = in.scale;
+  a.in_stride = field_units_per_rhs(P, ctx->g.Vh) * 16;
+  a.own = own ? own->data : nullptr;
+  a.own_scale = own ? own->scale : nullptr;
+  a.own_stride = a.in_stride;
+  a.out = out.data;
+  a.out_scale = out.scale;
+  a.out_stride = a.in_stride;
+  a.s = op.s;
+  a.norm_part = op.norm_part;
+  a.active = op.active;
+  const size_t Vh = ctx->g.Vh;
+  const int p = op.p_out;
+  const void* Kown = nullptr;
+  const void* Kout = nullptr;
+  if (P == DLMA_FP64) {
+    a.Ua = ctx->U64; a.Ub = nullptr;
+    Kown = op.own == 3 ? (const void*)(ctx->Ci64 + p * 36 * Vh) : (const void*)(ctx->C64 + p * 36 * Vh);
+    Kout = op.kout == 2 ? (const void*)(ctx->C64 + p * 36 * Vh) : (const void*)(ctx->Ci64 + p * 36 * Vh);
+  } else if (P == DLMA_FP32) {
+    a.Ua = ctx->U32; a.Ub = nullptr;
+    Kown = op.own == 3 ? (const void*)(ctx->Ci32 + p * 18 * Vh) : (const void*)(ctx->C32 + p * 18 * Vh);
+    Kout = op.kout == 2 ? (const void*)(ctx->C32 + p * 18 * Vh) : (const void*)(ctx->Ci32 + p * 18 * Vh);
+  } else {
+    a.Ua = ctx->U16a; a.Ub = ctx->U16b;
+    Kown = op.own == 3 ? (const void*)(ctx->Ci16 + p * 9 * Vh) : (const void*)(ctx->C16 + p * 9 * Vh);
+    Kout = op.kout == 2 ? (const void*)(ctx->C16 + p * 9 * Vh) : (const void*)(ctx->Ci16 + p * 9 * Vh);
+  }
+  a.Kown = Kown;
+  a.Kout = Kout;
+  int sx, sy;
+  hop_block(P, sx, sy);
+  dim3 blk(sx, sy);
+  dim3 grid((ctx->g.Vh + sx - 1) / sx, (out.nrhs + sy - 1) / sy);
+  if (nblocks_out) *nblocks_out = grid.x;
+  if (P == DLMA_FP64) dispatch<DLMA_FP64>(op, grid, blk, ctx->stream, a);
+  else if (P == DLMA_FP32) dispatch<DLMA_FP32>(op, grid, blk, ctx->stream, a);
+  else dispatch<DLMA_FP16S>(op, grid, blk, ctx->stream, a);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+dlma_status schur_apply(dlma_ctx* ctx, const Field& in, Field& tmp, Field& out, int dagger, const int* active,
+                        double* norm_part) {
+  HopOp A;
+  A.p_out = 1;
+  A.own = 0;
+  A.kout = 3;
+  A.g5_in = dagger;
+  A.active = active;
+  TRY(launch_hop(ctx, A, in, nullptr, tmp));
+  HopOp B;
+  B.p_out = 0;
+  B.own = 2;
+  B.kout = 0;
+  B.g5_hop = dagger;
+  B.s = -1.0;
+  B.active = active;
+  B.norm_part = norm_part;
+  TRY(launch_hop(ctx, B, tmp, &in, out));
+  return DLMA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// canonical complex128 <-> internal fields
+template <int P>
+__global__ void k_pack(Geom g, const double2* __restrict__ src, int full, int p, int nrhs, void* dst, float* scale) {
+  typedef typename PT<P>::R R;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  if (i >= g.Vh || j >= nrhs) return;
+  size_t site;
+  if (full) {
+    Coord c = eo_coords(g, p, i);
+    site = (size_t)j * g.V + lex_of(g, c.x, c.y, c.z, c.t);
+  } else {
+    site = (size_t)j * g.Vh + i;
+  }
+  const double2* s = src + site * 12;
+  Spinor<R> v;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    double2 e = s[k];
+    v.c[k / 3][k % 3] = cx<R>((R)e.x, (R)e.y);
+  }
+  size_t stride = field_units_per_rhs(P, g.Vh) * 16;
+  store_spinor<P>((char*)dst + j * stride, scale ? scale + (size_t)j * g.Vh : nullptr, g.Vh, i, v);
+}
+
+template <int P>
+__global__ void k_unpack(Geom g, const void* __restrict__ srcf, const float* __restrict__ scale, int full, int p,
+                         int nrhs, double2* dst) {
+  typedef typename PT<P>::R R;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y;
+  if (i >= g.Vh || j >= nrhs) return;
+  size_t stride = field_units_per_rhs(P, g.Vh) * 16;
+  Spinor<R> v = load_spinor<P>((const char*)srcf + j * stride, scale ? scale + (size_t)j * g.Vh : nullptr, g.Vh, i);
+  size_t site;
+  if (full) {
+    Coord c = eo_coords(g, p, i);
+    site = (size_t)j * g.V + lex_of(g, c.x, c.y, c.z, c.t);
+  } else {
+    site = (size_t)j * g.Vh + i;
+  }
+  double2* d = dst + site * 12;
+#pragma unroll
+  for (int k = 0; k < 12; k++) d[k] = make_double2((double)v.c[k / 3][k % 3].re, (double)v.c[k / 3][k % 3].im);
+}
+
+dlma_status pack_parity(dlma_ctx* ctx, const double* src, int full, int p, Field& f) {
+  dim3 grid((ctx->g.Vh + 127) / 128, f.nrhs);
+  if (f.prec == DLMA_FP64) k_pack<DLMA_FP64><<<grid, 128, 0, ctx->stream>>>(ctx->g, (const double2*)src, full, p, f.nrhs, f.data, f.scale);
+  else if (f.prec == DLMA_FP32) k_pack<DLMA_FP32><<<grid, 128, 0, ctx->stream>>>(ctx->g, (const double2*)src, full, p, f.nrhs, f.data, f.scale);
+  else k_pack<DLMA_FP16S><<<grid, 128, 0, ctx->stream>>>(ctx->g, (const double2*)src, full, p, f.nrhs, f.data, f.scale);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+dlma_status unpack_parity(dlma_ctx* ctx, const Field& f, int full, int p, double* dst) {
+  dim3 grid((ctx->g.Vh + 127) / 128, f.nrhs);
+  if (f.prec == DLMA_FP64) k_unpack<DLMA_FP64><<<grid, 128, 0, ctx->stream>>>(ctx->g, f.data, f.scale, full, p, f.nrhs, (double2*)dst);
+  else if (f.prec == DLMA_FP32) k_unpack<DLMA_FP32><<<grid, 128, 0, ctx->stream>>>(ctx->g, f.data, f.scale, full, p, f.nrhs, (double2*)dst);
+  else k_unpack<DLMA_FP16S><<<grid, 128, 0, ctx->stream>>>(ctx->g, f.data, f.scale, full, p, f.nrhs, (double2*)dst);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: operator applications
+static dlma_status check_ready(dlma_ctx* ctx) {
+  if (!ctx) return DLMA_ERR_INVALID_ARG;
+  if (!ctx->have_gauge || !ctx->have_params)
+    return set_err(ctx, DLMA_ERR_STATE, "gauge field and parameters must be set first");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return set_err(ctx, DLMA_ERR_CUDA, "cudaSetDevice failed");
+  return DLMA_OK;
+}
+
+extern "C" dlma_status dlma_apply_Dw(dlma_ctx* ctx, const double* in, double* out, int nrhs, dlma_prec prec,
+                                     dlma_mem mem) {
+  TRY(check_ready(ctx));
+  if (!in || !out || nrhs < 1 || prec < DLMA_FP64 || prec > DLMA_FP16S)
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_apply_Dw");
+  size_t bytes = (size_t)nrhs * ctx->g.V * 12 * 16;
+  const double* din;
+  TRY(copy_in(ctx, WS_IN, in, bytes, mem, &din));
+  double* dout = out;
+  if (mem == DLMA_MEM_HOST) TRY(workT(ctx, WS_OUT, bytes / 8, &dout));
+  Field fe, fo, re, ro;
+  TRY(field_alloc(ctx, WS_T0, prec, nrhs, &fe));
+  TRY(field_alloc(ctx, WS_T1, prec, nrhs, &fo));
+  TRY(field_alloc(ctx, WS_T2, prec, 2 * nrhs, &re));
+  ro = re;
+  ro.nrhs = nrhs;
+  ro.data = (char*)re.data + field_units_per_rhs(prec, ctx->g.Vh) * 16 * nrhs;
+  if (prec == DLMA_FP16S) ro.scale = re.scale + (size_t)nrhs * ctx->g.Vh;
+  re.nrhs = nrhs;
+  if (prec == DLMA_FP16S) {
+    // two fields share one buffer: keep their scale arrays apart
+    re.scale = (float*)((char*)re.data + field_units_per_rhs(prec, ctx->g.Vh) * 16 * 2 * nrhs);
+    ro.scale = re.scale + (size_t)nrhs * ctx->g.Vh;
+  }
+  TRY(pack_parity(ctx, din, 1, 0, fe));
+  TRY(pack_parity(ctx, din, 1, 1, fo));
+  HopOp op;
+  op.own = 2;
+  op.kout = 0;
+  op.p_out = 0;
+  TRY(launch_hop(ctx, op, fo, &fe, re));
+  op.p_out = 1;
+  TRY(launch_hop(ctx, op, fe, &fo, ro));
+  TRY(unpack_parity(ctx, re, 1, 0, dout));
+  TRY(unpack_parity(ctx, ro, 1, 1, dout));
+  if (mem == DLMA_MEM_HOST) TRY(copy_out(ctx, out, dout, bytes, mem));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return DLMA_OK;
+}
+
+extern "C" dlma_status dlma_apply_schur(dlma_ctx* ctx, const double* in, double* out, int nrhs, int dagger,
+                                        dlma_prec prec, dlma_mem mem) {
+  TRY(check_ready(ctx));
+  if (!in || !out || nrhs < 1 || prec < DLMA_FP64 || prec > DLMA_FP16S)
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_apply_schur");
+  size_t bytes = (size_t)nrhs * ctx->g.Vh * 12 * 16;
+  const double* din;
+  TRY(copy_in(ctx, WS_IN, in, bytes, mem, &din));
+  double* dout = out;
+  if (mem == DLMA_MEM_HOST) TRY(workT(ctx, WS_OUT, bytes / 8, &dout));
+  Field fe, tmp, res;
+  TRY(field_alloc(ctx, WS_T0, prec, nrhs, &fe));
+  TRY(field_alloc(ctx, WS_T1, prec, nrhs, &tmp));
+  TRY(field_alloc(ctx, WS_T2, prec, nrhs, &res));
+  TRY(pack_parity(ctx, din, 0, 0, fe));
+  EvTimer ev;
+  CU(cudaEventCreate(&ev.a));
+  CU(cudaEventCreate(&ev.b));
+  CU(cudaEventRecord(ev.a, ctx->stream));
+  TRY(schur_apply(ctx, fe, tmp, res, dagger ? 1 : 0, nullptr, nullptr));
+  CU(cudaEventRecord(ev.b, ctx->stream));
+  TRY(unpack_parity(ctx, res, 0, 0, dout));
+  if (mem == DLMA_MEM_HOST) TRY(copy_out(ctx, out, dout, bytes, mem));
+  CU(cudaStreamSynchronize(ctx->stream));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ev.a, ev.b);
+  ctx->timing[0] = ms;
+  ctx->timing[1] = ms;
+  ctx->timing[2] = 2;
+  cudaEventDestroy(ev.a);
+  cudaEventDestroy(ev.b);
+  return DLMA_OK;
+}
