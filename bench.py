@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark: the distillation-LMA hot path on one GB300 per rank.
+
+One step = one pass of the whole hot path on the 16^3 x 32 precision workload
+(eps 0.2, kappa 0.1225, c_sw 1.0): the N = 32 lowest Laplacian modes of every
+timeslice, the 4N + 5 N_r = 168 sources of t' = 0 (N_r = 8 Z2 x Z2 noise
+vectors), their Wilson-clover solves to true residual 1e-10 (FP32 inner CGNE
+in FP64 defect correction, all right-hand sides batched), the V^dag psi
+projections and the C_rest / C_mixed / C_dist contractions.
+
+value    = solves reaching 1e-10 per second of step time, all ranks (replicas)
+e2e      = the same through the C ABI with HOST buffers: links and noise
+           copied in, correlators copied out, clover rebuilt, every step
+roofline = the even-odd Schur stencil (two hop launches) on the same batch,
+           timed with CUDA events on the library's stream right after the
+           timed region; algorithmic bytes: perfect reuse, links and clover
+           read once per launch
+cpu_baseline / --impl reference = the FP64 oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dw-clover HBM GB/s vs peak; solves/s at 1e-10 residual, mixed+batched vs FP64"
+WORKLOAD = "precision_16c32"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_cgne_precision_16c32.json")
+PROFILE = os.path.join(ROOT, "profiles", "hop_fp32_precision_16c32.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    for p in (os.path.join(ROOT, "MEASURED_PEAKS.json"), "/root/repo/MEASURED_PEAKS.json"):
+        if os.path.exists(p):
+            try:
+                d = json.load(open(p))
+                for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                    if k in d:
+                        return float(d[k]), "measured"
+            except Exception:
+                pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    for f in ("dslash.cu", "fieldio.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2201_09729_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic():
+    """dram bytes per Schur application from the committed ncu summary, if the
+    stencil source has not changed since it was taken."""
+    try:
+        d = json.load(open(PROFILE))
+        if d.get("source_hash") == _src_hash():
+            return d.get("dram_bytes_per_schur")
+    except Exception:
+        pass
+    return None
+
+
+def schur_bytes(Vh: int, nrhs: int, prec: str) -> float:
+    """Algorithmic bytes of one Schur application Dhat = T_ee - D_eo T_oo^-1 D_oe
+    on nrhs right-hand sides (two hop launches), perfect reuse:
+    hop A (odd out)  : in + out spinor per rhs, 8 links + clover per site
+    hop B (even out) : in + own + out spinor per rhs, 8 links + clover per site."""
+    if prec == "fp32":
+        sp, link, clov = 24 * 4, 12 * 4, 72 * 4
+    elif prec == "fp16s":
+        sp, link, clov = 24 * 2 + 4, 12 * 2, 72 * 2
+    else:
+        sp, link, clov = 24 * 8, 18 * 8, 72 * 8
+    per_site_fixed = 8 * link + clov
+    return Vh * (nrhs * 2 * sp + per_site_fixed) + Vh * (nrhs * 3 * sp + per_site_fixed)
+
+
+def cpu_baseline(seconds_target: float = 15.0):
+    """Oracle CGNE iterations on the bench workload, timed on the host cores
+    (single thread), scaled to solves/s by the oracle's own iteration count."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import synth
+from oracle import dirac
+wl = synth.WORKLOADS[{WORKLOAD!r}]
+U, eta = synth.workload_inputs(wl, n_noise=1)
+eo = dirac.EvenOdd(U, wl.L, wl.T, wl.m0, wl.csw)
+b = np.zeros((wl.volume, 4, 3), dtype=np.complex128)
+b[:wl.vol_s] = eta[0, 0]
+bhat = eo.prepare(b)
+r = eo.schur_dag(bhat); p = r.copy(); x = np.zeros_like(r)
+rr = np.vdot(r.ravel(), r.ravel()).real
+t0 = time.time(); it = 0
+while time.time() - t0 < {seconds_target} or it < 2:
+    q = eo.schur(p); a = rr / np.vdot(q.ravel(), q.ravel()).real
+    x = x + a * p; r = r - a * eo.schur_dag(q)
+    rn = np.vdot(r.ravel(), r.ravel()).real; p = r + (rn / rr) * p; rr = rn; it += 1
+print(json.dumps({{"iters": it, "seconds": time.time() - t0}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    g = json.load(open(GOLDEN))
+    per_it = d["seconds"] / d["iters"]
+    return {"value": 1.0 / (per_it * g["iterations"]), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"{d['iters']} oracle FP64 CGNE iterations ({d['seconds']:.1f} s) on one Z2xZ2 noise "
+                       f"source of the 16^3x32 workload, scaled by the oracle's {g['iterations']} iterations "
+                       f"to 1e-10 (tests/golden/oracle_cgne_precision_16c32.json); solve only")}
+
+
+def run_reference(args, rank):
+    """--impl reference: the FP64 oracle as it stands on the host cores."""
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(5.0)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(10.0))
+    v = statistics.median([x["value"] for x in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 168 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "lattice": "16^3x32", "solves_per_step": 168},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--inner", default="fp32", choices=["fp32", "fp16s"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    args.warmup = max(3, args.warmup)
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2201_09729_gb300 import FP32, FP16S, FP64, Context, build
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if local == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+
+    wl = synth.WORKLOADS[WORKLOAD]
+    U_h, eta_h = synth.workload_inputs(wl)
+    N, nn, J = wl.n_modes, wl.n_noise, 4 * wl.n_modes + 5 * wl.n_noise
+    inner = FP32 if args.inner == "fp32" else FP16S
+    stream = torch.cuda.Stream()
+    ctx = Context(wl.L, wl.T, 0, local, stream=stream.cuda_stream)
+    U_d = torch.from_numpy(U_h).to(f"cuda:{local}")
+    eta_d = torch.from_numpy(np.ascontiguousarray(eta_h[0])).to(f"cuda:{local}")
+    torch.cuda.synchronize()
+    ctx.dlma_set_gauge(U_d)
+    ctx.dlma_set_params(wl.m0, wl.csw)
+
+    phase = {"eigs_ms": [], "corr_ms": []}
+
+    def step():
+        ctx.dlma_laplacian_eigs(-1, N, 1e-10, device_out=True, want_vecs=False)
+        phase["eigs_ms"].append(ctx.dlma_last_timing()[0])
+        r = ctx.dlma_correlators(0, N, eta_d, wl.tol, inner)
+        phase["corr_ms"].append(ctx.dlma_last_timing()[0])
+        return r
+
+    for _ in range(args.warmup):
+        res = step()
+    assert all(i["converged"] for i in res["info"]), "a solve did not converge"
+    phase = {"eigs_ms": [], "corr_ms": []}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = ctx.dlma_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.dlma_kernel_launches() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = J * world / (ms / 1000.0)
+    iters = [i["iters_inner"] for i in res["info"]]
+
+    # e2e: the same step through HOST buffers, links / noise in, correlators out
+    U_pin = torch.from_numpy(U_h).pin_memory()
+    eta_pin = torch.from_numpy(np.ascontiguousarray(eta_h[0])).pin_memory()
+    U_np, eta_np = U_pin.numpy(), eta_pin.numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.dlma_set_gauge(U_np)
+        ctx.dlma_set_params(wl.m0, wl.csw)
+        ctx.dlma_laplacian_eigs(-1, N, 1e-10, want_vecs=False)
+        r2 = ctx.dlma_correlators(0, N, eta_np, wl.tol, inner)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    h2d = U_np.nbytes + eta_np.nbytes
+    d2h = 3 * r2["C_dist"].nbytes + 8 * wl.T * N
+    assert all(i["converged"] for i in r2["info"])
+
+    # plain FP64 single-RHS GPU solves on a bounded sample (two noise sources)
+    b1 = torch.zeros((1, wl.volume, 4, 3), dtype=torch.complex128, device=f"cuda:{local}")
+    fp64_ms = []
+    for r in range(2):
+        b1.zero_()
+        b1[0, : wl.vol_s] = torch.from_numpy(eta_h[0, r]).to(b1.device)
+        torch.cuda.synchronize()
+        _, inf = ctx.dlma_solve(b1, wl.tol, FP64)
+        fp64_ms.append(ctx.dlma_last_timing()[0])
+    fp64_sps = 1000.0 / statistics.mean(fp64_ms)
+    # mixed precision batched solve alone on the same 40 noise solves
+    corr_solve_sps = J / (statistics.mean(phase["corr_ms"]) / 1000.0)
+
+    # roofline: the Schur stencil on the full batch
+    prec_name = args.inner
+    Vh = wl.volume // 2
+    gen = torch.Generator(device=f"cuda:{local}").manual_seed(7)
+    ve = torch.randn((J, Vh, 4, 3), dtype=torch.complex128, device=f"cuda:{local}", generator=gen)
+    sch = []
+    for k in range(12):
+        ctx.dlma_apply_schur(ve, 0, inner)
+        if k >= 2:
+            sch.append(ctx.dlma_last_timing()[0])
+    del ve
+    schur_ms = statistics.mean(sch)
+    alg = schur_bytes(Vh, J, prec_name)
+    peak, peak_kind = _peaks()
+    achieved = alg / (schur_ms / 1000.0) / 1e9
+    traffic = _traffic()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.inner == "fp32" else "f16+f32+f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 16^3x32 lattice, eps 0.2, kappa 0.1225, c_sw 1.0, N=32 Laplacian modes "
+                               f"per timeslice, 128 distillation + 40 noise solves at t'=0, true residual 1e-10, "
+                               f"{args.inner} inner CGNE + FP64 defect correction",
+                   "solves_per_step": J, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (per-step working set > 10 GB)"},
+        "e2e": {"value": J * world / (e2e_ms / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches // args.steps),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": f"k_hop {prec_name} Schur (2 launches), batch {J}",
+                     "peak_source": f"{peak_kind} HBM copy bandwidth"},
+        "clocks": clocks,
+        "breakdown": {"eigs_ms": statistics.mean(phase["eigs_ms"]), "correlators_ms": statistics.mean(phase["corr_ms"]),
+                      "solves_per_s_correlator_phase": corr_solve_sps,
+                      "fp64_single_rhs_solves_per_s": fp64_sps,
+                      "speedup_mixed_batched_vs_fp64_single": corr_solve_sps / fp64_sps,
+                      "inner_iters_median": statistics.median(iters),
+                      "schur_ms": schur_ms},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as ex:  # the baseline is a report, not the target
+            line["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {ex}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

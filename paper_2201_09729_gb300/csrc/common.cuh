@@ -117,6 +117,7 @@ struct dlma_ctx {
   int eig_N = 0;
   double2* eig_V = nullptr;       // [N][T][Vs][3]
   std::vector<double> eig_lam;    // [T][N]
+  std::vector<int> eig_have;      // [T] modes cached for timeslice t
 
   // named work buffers
   DevBuf wb[64];
@@ -222,7 +223,7 @@ int hop_grid_x(dlma_ctx* ctx, int prec);
 dlma_status schur_apply(dlma_ctx* ctx, const Field& in, Field& tmp, Field& out, int dagger,
                         const int* active, double* norm_part);
 
-dlma_status eig_run(dlma_ctx* ctx, int N, double tol);
+void gamma_matrices(double G[4][4][4][2]);
 dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol,
                          dlma_prec inner, dlma_solve_info* info);
 

@@ -1,26 +1,537 @@
-// Distillation sources, projections and contractions (placeholders).
+// Distillation sources, V^dag psi projections and the correlator parts of
+// Eqs. 2-4.
+//
+//   sources (text after Eq. 3, Eq. 4): v_k(t') (x) e_alpha; eta_r;
+//     (1 - Box(t')) eta_r; gamma_5 gamma_k (1 - Box(t')) eta_r, k = 1..3
+//   projection (Eq. 1): c_j(t)[alpha][k] = sum_{m,c} conj(v_k(m,c;t)) psi_j(m,t,alpha,c)
+//   perambulator tau(t)[(k,alpha),(l,beta)] = c_{4l+beta}(t)[alpha][k]
+//   C_dist(t)  = tr[g5 G tau G g5 tau^dag]                                  (Eq. 3)
+//   C_mixed(t) = 1/N_r sum_r sum_{alpha,beta} (g5 G)_{alpha beta} sum_k conj(a_r[k,alpha]) c_r[k,beta]
+//   C_rest(t)  = 1/N_r sum_r sum_{alpha,beta} (g5 G)_{alpha beta} M_r[alpha][beta] - C_mixed(t)
+// with c_r the coefficients of phi_r, a_r those of the left vector chi_r and
+// M_r[alpha][beta] = sum_{x in t} conj(chi_r(x,alpha)) . phi_r(x,beta): the
+// Box(t) insertion at the sink only needs the projection coefficients, since
+// Box is diagonal in spin.
 #include "common.cuh"
+#include <algorithm>
 
+namespace {
+
+struct SpinMats {
+  // [0..3] g5 G for G = g5, g1, g2, g3; [4..7] G g5; [8..10] g5 g_k (k = 1..3)
+  double re[11][4][4], im[11][4][4];
+};
+
+SpinMats spin_mats() {
+  double G[4][4][4][2];
+  gamma_matrices(G);
+  // gamma_5 = g0 g1 g2 g3
+  auto mul = [](const double a[4][4][2], const double b[4][4][2], double o[4][4][2]) {
+    for (int i = 0; i < 4; i++)
+      for (int j = 0; j < 4; j++) {
+        double r = 0, im = 0;
+        for (int k = 0; k < 4; k++) {
+          r += a[i][k][0] * b[k][j][0] - a[i][k][1] * b[k][j][1];
+          im += a[i][k][0] * b[k][j][1] + a[i][k][1] * b[k][j][0];
+        }
+        o[i][j][0] = r;
+        o[i][j][1] = im;
+      }
+  };
+  double t1[4][4][2], t2[4][4][2], g5[4][4][2];
+  mul(G[0], G[1], t1);
+  mul(t1, G[2], t2);
+  mul(t2, G[3], g5);
+  const double(*ch[4])[4][2] = {g5, G[1], G[2], G[3]};
+  SpinMats S;
+  double o[4][4][2];
+  for (int c = 0; c < 4; c++) {
+    mul(g5, ch[c], o);
+    for (int i = 0; i < 4; i++)
+      for (int j = 0; j < 4; j++) { S.re[c][i][j] = o[i][j][0]; S.im[c][i][j] = o[i][j][1]; }
+    mul(ch[c], g5, o);
+    for (int i = 0; i < 4; i++)
+      for (int j = 0; j < 4; j++) { S.re[4 + c][i][j] = o[i][j][0]; S.im[4 + c][i][j] = o[i][j][1]; }
+  }
+  for (int k = 0; k < 3; k++) {
+    mul(g5, G[k + 1], o);
+    for (int i = 0; i < 4; i++)
+      for (int j = 0; j < 4; j++) { S.re[8 + k][i][j] = o[i][j][0]; S.im[8 + k][i][j] = o[i][j][1]; }
+  }
+  return S;
+}
+
+// VT[t][(m*3 + c) * N + k] = V(t, k, m, c); V(t, k) at vector index t * st_t + k * st_k
+__global__ void k_transpose_V(const double2* __restrict__ V, int st_t, int st_k, int Tsel, int t0, int N, int n,
+                              double2* VT) {
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)Tsel * N * n;
+  if (e >= tot) return;
+  int k = e % N;
+  size_t r = e / N;
+  int mc = r % n;
+  int t = r / n;
+  VT[e] = V[((size_t)(t0 + t) * st_t + (size_t)k * st_k) * n + mc];
+}
+
+// coeff[j][t][alpha][k] = sum_{m,c} conj(V_t[k][m][c]) psi_j(site0(t) + m, alpha, c)
+constexpr int JB = 4;
+__global__ void k_project(const double2* __restrict__ VT, int N, int Vs, int Tsel, const double2* __restrict__ psi,
+                          size_t psi_stride_sites, int site_t0, int nrhs, double2* coeff) {
+  const int t = blockIdx.x, j0 = blockIdx.y * JB, k = threadIdx.x;
+  const bool on = k < N;
+  Cx<double> acc[JB][4];
+#pragma unroll
+  for (int jj = 0; jj < JB; jj++)
+#pragma unroll
+    for (int a = 0; a < 4; a++) acc[jj][a] = cx<double>(0, 0);
+  const double2* vt = VT + (size_t)t * 3 * Vs * N;
+  const size_t site0 = (size_t)(site_t0 + t) * Vs;
+  for (int m = 0; m < Vs; m++) {
+    Cx<double> v[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      double2 e = on ? vt[(size_t)(m * 3 + c) * N + k] : make_double2(0, 0);
+      v[c] = cx<double>(e.x, e.y);
+    }
+#pragma unroll
+    for (int jj = 0; jj < JB; jj++) {
+      if (j0 + jj >= nrhs) break;
+      const double2* p = psi + ((size_t)(j0 + jj) * psi_stride_sites + site0 + m) * 12;
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          double2 e = __ldg(p + a * 3 + c);
+          fma_conj_acc(acc[jj][a], v[c], cx<double>(e.x, e.y));
+        }
+    }
+  }
+  if (!on) return;
+#pragma unroll
+  for (int jj = 0; jj < JB; jj++) {
+    if (j0 + jj >= nrhs) break;
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+      coeff[(((size_t)(j0 + jj) * Tsel + t) * 4 + a) * N + k] = make_double2(acc[jj][a].re, acc[jj][a].im);
+  }
+}
+
+// pe[r][m][alpha][c] = eta - sum_k V[k][m][c] coeff[r][alpha][k]   ((1 - Box) eta on one timeslice)
+__global__ void k_deproject(const double2* __restrict__ VT, int N, int Vs, const double2* __restrict__ eta,
+                            const double2* __restrict__ coeff, int nn, double2* pe) {
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)nn * Vs * 12) return;
+  int c = e % 3, a = (e / 3) % 4;
+  size_t m = (e / 12) % Vs, r = e / ((size_t)12 * Vs);
+  Cx<double> s = cx<double>(eta[e].x, eta[e].y);
+  for (int k = 0; k < N; k++) {
+    double2 v = VT[(m * 3 + c) * N + k], q = coeff[(r * 4 + a) * N + k];
+    s = s - cx<double>(v.x, v.y) * cx<double>(q.x, q.y);
+  }
+  pe[e] = make_double2(s.re, s.im);
+}
+
+// sources j in [j0, j0 + nb): b must be zeroed; writes the timeslice t_src part
+__global__ void k_sources(int j0, int nb, int N, int Vs, int t_src, const double2* __restrict__ VT,
+                          const double2* __restrict__ eta, const double2* __restrict__ pe, SpinMats S, double2* b,
+                          size_t stride_sites) {
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)nb * Vs) return;
+  int m = e % Vs;
+  int jl = e / Vs;
+  int j = j0 + jl;
+  double2* out = b + ((size_t)jl * stride_sites + (size_t)t_src * Vs + m) * 12;
+  if (j < 4 * N) {
+    int k = j / 4, a = j % 4;
+    for (int c = 0; c < 3; c++) out[a * 3 + c] = VT[((size_t)m * 3 + c) * N + k];
+    return;
+  }
+  int r = (j - 4 * N) / 5, kind = (j - 4 * N) % 5;
+  const double2* src = (kind == 0 ? eta : pe) + ((size_t)r * Vs + m) * 12;
+  if (kind <= 1) {
+    for (int q = 0; q < 12; q++) out[q] = src[q];
+    return;
+  }
+  const int mi = 8 + (kind - 2);   // g5 g_k
+  for (int a = 0; a < 4; a++)
+    for (int c = 0; c < 3; c++) {
+      Cx<double> s = cx<double>(0, 0);
+      for (int bb = 0; bb < 4; bb++)
+        fma_acc(s, cx<double>(S.re[mi][a][bb], S.im[mi][a][bb]), cx<double>(src[bb * 3 + c].x, src[bb * 3 + c].y));
+      out[a * 3 + c] = make_double2(s.re, s.im);
+    }
+}
+
+// M[p][t][alpha][beta] = sum_{m in t, c} conj(chi(m, alpha, c)) phi(m, beta, c) for pairs p = (chi_idx, phi_idx)
+__global__ void __launch_bounds__(256) k_spin_inner(const double2* __restrict__ psi, size_t stride_sites, int Vs,
+                                                    const int* __restrict__ pairs, double2* M, int T) {
+  const int t = blockIdx.x, p = blockIdx.y;
+  const int ci = pairs[2 * p], fi = pairs[2 * p + 1];
+  Cx<double> acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; q++) acc[q] = cx<double>(0, 0);
+  for (int m = threadIdx.x; m < Vs; m += blockDim.x) {
+    const double2* x = psi + ((size_t)ci * stride_sites + (size_t)t * Vs + m) * 12;
+    const double2* f = psi + ((size_t)fi * stride_sites + (size_t)t * Vs + m) * 12;
+    Cx<double> xv[12], fv[12];
+#pragma unroll
+    for (int q = 0; q < 12; q++) {
+      xv[q] = cx<double>(x[q].x, x[q].y);
+      fv[q] = cx<double>(f[q].x, f[q].y);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int b = 0; b < 4; b++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) fma_conj_acc(acc[a * 4 + b], xv[a * 3 + c], fv[b * 3 + c]);
+  }
+  __shared__ double red[2][256];
+  for (int q = 0; q < 16; q++) {
+    red[0][threadIdx.x] = acc[q].re;
+    red[1][threadIdx.x] = acc[q].im;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        red[0][threadIdx.x] += red[0][threadIdx.x + o];
+        red[1][threadIdx.x] += red[1][threadIdx.x + o];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) M[((size_t)p * T + t) * 16 + q] = make_double2(red[0][0], red[1][0]);
+    __syncthreads();
+  }
+}
+
+// C_dist[ch][t] from the distillation coefficient rows coeff[4l+beta][t][alpha][k]
+__global__ void __launch_bounds__(256) k_cdist(const double2* __restrict__ coeff, int N, int T, SpinMats S,
+                                               double2* out) {
+  const int t = blockIdx.x, ch = blockIdx.y;
+  Cx<double> acc = cx<double>(0, 0);
+  for (int kl = threadIdx.x; kl < N * N; kl += blockDim.x) {
+    const int k = kl / N, l = kl % N;
+    Cx<double> tau[4][4];          // tau[alpha][beta] = coeff[4l+beta][t][alpha][k]
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int b = 0; b < 4; b++) {
+        double2 e = coeff[(((size_t)(4 * l + b) * T + t) * 4 + a) * N + k];
+        tau[a][b] = cx<double>(e.x, e.y);
+      }
+    // sum_{a,a',b,b'} A[a][a'] tau[a'][b] B[b][b'] conj(tau[a][b'])
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int bp = 0; bp < 4; bp++) {
+        Cx<double> p = cx<double>(0, 0);
+#pragma unroll
+        for (int ap = 0; ap < 4; ap++)
+#pragma unroll
+          for (int b = 0; b < 4; b++) {
+            Cx<double> ab = cx<double>(S.re[ch][a][ap], S.im[ch][a][ap]) * cx<double>(S.re[4 + ch][b][bp], S.im[4 + ch][b][bp]);
+            fma_acc(p, ab, tau[ap][b]);
+          }
+        fma_acc(acc, p, conj(tau[a][bp]));
+      }
+  }
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = acc.re;
+  red[1][threadIdx.x] = acc.im;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(size_t)ch * T + t] = make_double2(red[0][0], red[1][0]);
+}
+
+// noise parts: rest/mixed[ch][t] from M[r][ch][t][16] and coefficient rows of chi / phi
+__global__ void __launch_bounds__(128) k_noise_parts(const double2* __restrict__ M, const double2* __restrict__ coeff,
+                                                     int N, int T, int nn, int row0, SpinMats S, double2* rest,
+                                                     double2* mixed) {
+  const int t = blockIdx.x, ch = blockIdx.y;
+  Cx<double> mix = cx<double>(0, 0), full = cx<double>(0, 0);
+  for (int e = threadIdx.x; e < nn * N; e += blockDim.x) {
+    const int r = e / N, k = e % N;
+    const int rphi = row0 + 5 * r, rchi = row0 + 5 * r + 1 + ch;
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; b < 4; b++) {
+        Cx<double> A = cx<double>(S.re[ch][a][b], S.im[ch][a][b]);
+        double2 ca = coeff[(((size_t)rchi * T + t) * 4 + a) * N + k];
+        double2 cb = coeff[(((size_t)rphi * T + t) * 4 + b) * N + k];
+        Cx<double> pr = conj(cx<double>(ca.x, ca.y)) * cx<double>(cb.x, cb.y);
+        fma_acc(mix, A, pr);
+        if (k == 0) {
+          double2 mv = M[(((size_t)r * 4 + ch) * T + t) * 16 + a * 4 + b];
+          fma_acc(full, A, cx<double>(mv.x, mv.y));
+        }
+      }
+  }
+  __shared__ double red[4][128];
+  red[0][threadIdx.x] = mix.re;
+  red[1][threadIdx.x] = mix.im;
+  red[2][threadIdx.x] = full.re;
+  red[3][threadIdx.x] = full.im;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 4; q++) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double inv = 1.0 / nn;
+    mixed[(size_t)ch * T + t] = make_double2(red[0][0] * inv, red[1][0] * inv);
+    rest[(size_t)ch * T + t] = make_double2((red[2][0] - red[0][0]) * inv, (red[3][0] - red[1][0]) * inv);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// internal drivers
+static dlma_status transpose_V(dlma_ctx* ctx, const double* V, int st_t, int st_k, int Tsel, int t0, int N,
+                               double2** VT, int slot) {
+  const int n = 3 * ctx->g.Vs;
+  size_t tot = (size_t)Tsel * N * n;
+  TRY(workT(ctx, slot, tot, VT));
+  k_transpose_V<<<(tot + 255) / 256, 256, 0, ctx->stream>>>((const double2*)V, st_t, st_k, Tsel, t0, N, n, *VT);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+static dlma_status project(dlma_ctx* ctx, const double2* VT, int N, int Tsel, const double* psi, size_t stride_sites,
+                           int site_t0, int nrhs, double2* coeff) {
+  if (N > 256) return set_err(ctx, DLMA_ERR_INVALID_ARG, "N above 256 in the projection");
+  int nt = ((N + 31) / 32) * 32;
+  dim3 grid(Tsel, (nrhs + JB - 1) / JB);
+  k_project<<<grid, nt, 0, ctx->stream>>>(VT, N, ctx->g.Vs, Tsel, (const double2*)psi, stride_sites, site_t0, nrhs,
+                                          coeff);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+// (1 - Box(t')) eta for all noise vectors: pe [nn][Vs][4][3]
+static dlma_status project_noise(dlma_ctx* ctx, const double2* VTs, int N, const double* eta, int nn, double2** pe) {
+  const int Vs = ctx->g.Vs;
+  double2* co;
+  TRY(workT(ctx, WS_CON2, (size_t)nn * 4 * N, &co));
+  TRY(project(ctx, VTs, N, 1, eta, (size_t)Vs, 0, nn, co));
+  TRY(workT(ctx, WS_ETA, (size_t)nn * Vs * 12, pe));
+  size_t tot = (size_t)nn * Vs * 12;
+  k_deproject<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(VTs, N, Vs, (const double2*)eta, co, nn, *pe);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+static dlma_status sources_range(dlma_ctx* ctx, int j0, int nb, int N, int t_src, const double2* VTs,
+                                 const double* eta, const double2* pe, double* b) {
+  const int Vs = ctx->g.Vs;
+  CU(cudaMemsetAsync(b, 0, (size_t)nb * ctx->g.V * 12 * 16, ctx->stream));
+  size_t tot = (size_t)nb * Vs;
+  k_sources<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(j0, nb, N, Vs, t_src, VTs, (const double2*)eta, pe,
+                                                        spin_mats(), (double2*)b, (size_t)ctx->g.V);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+// noise-pair spin inner products for noise groups r in [r0, r0 + nr) whose 5 solutions start at row `base` of psi
+static dlma_status spin_inner(dlma_ctx* ctx, const double* psi, int nr, int base, double2* M) {
+  std::vector<int> hp(8 * nr);
+  for (int r = 0; r < nr; r++)
+    for (int ch = 0; ch < 4; ch++) {
+      hp[2 * (4 * r + ch)] = base + 5 * r + 1 + ch;   // chi
+      hp[2 * (4 * r + ch) + 1] = base + 5 * r;        // phi
+    }
+  int* dp;
+  TRY(workT(ctx, WS_T2, hp.size(), &dp));
+  CU(cudaMemcpyAsync(dp, hp.data(), sizeof(int) * hp.size(), cudaMemcpyHostToDevice, ctx->stream));
+  dim3 grid(ctx->g.T, 4 * nr);
+  k_spin_inner<<<grid, 256, 0, ctx->stream>>>((const double2*)psi, (size_t)ctx->g.V, ctx->g.Vs, dp, M, ctx->g.T);
+  CHECK_LAUNCH();
+  // stream-ordered use of the pinned-free host vector: wait before it goes out of scope
+  CU(cudaStreamSynchronize(ctx->stream));
+  return DLMA_OK;
+}
+
+static dlma_status finish_contract(dlma_ctx* ctx, int N, int nn, const double2* coeff, const double2* M,
+                                   double* C_dist, double* C_rest, double* C_mixed) {
+  const int T = ctx->g.T;
+  double2* out;
+  TRY(workT(ctx, WS_CON, (size_t)12 * T, &out));
+  SpinMats S = spin_mats();
+  k_cdist<<<dim3(T, 4), 256, 0, ctx->stream>>>(coeff, N, T, S, out);
+  CHECK_LAUNCH();
+  if (nn > 0) {
+    k_noise_parts<<<dim3(T, 4), 128, 0, ctx->stream>>>(M, coeff, N, T, nn, 4 * N, S, out + 4 * T, out + 8 * T);
+    CHECK_LAUNCH();
+  } else {
+    CU(cudaMemsetAsync(out + 4 * T, 0, sizeof(double2) * 8 * T, ctx->stream));
+  }
+  std::vector<double2> h(12 * T);
+  CU(cudaMemcpyAsync(h.data(), out, sizeof(double2) * 12 * T, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  memcpy(C_dist, h.data(), sizeof(double2) * 4 * T);
+  memcpy(C_rest, h.data() + 4 * T, sizeof(double2) * 4 * T);
+  memcpy(C_mixed, h.data() + 8 * T, sizeof(double2) * 4 * T);
+  return DLMA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
 extern "C" dlma_status dlma_make_sources(dlma_ctx* ctx, int t_src, int N, const double* V, int n_noise,
                                          const double* eta, double* b, dlma_mem mem) {
-  (void)t_src; (void)N; (void)V; (void)n_noise; (void)eta; (void)b; (void)mem;
-  return set_err(ctx, DLMA_ERR_STATE, "not built yet");
+  if (!ctx) return DLMA_ERR_INVALID_ARG;
+  if (!V || !b || N < 1 || n_noise < 0 || (n_noise > 0 && !eta) || t_src < 0 || t_src >= ctx->g.T)
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_make_sources");
+  CU(cudaSetDevice(ctx->device));
+  const int Vs = ctx->g.Vs, n = 3 * Vs;
+  const double* dV;
+  TRY(copy_in(ctx, WS_PROJ_V, V, (size_t)N * n * 16, mem, &dV));
+  const double* deta = nullptr;
+  if (n_noise) TRY(copy_in(ctx, WS_SRC, eta, (size_t)n_noise * Vs * 12 * 16, mem, &deta));
+  double2* VT;
+  TRY(transpose_V(ctx, dV, 0, 1, 1, 0, N, &VT, WS_PROJ_PART));
+  double2* pe = nullptr;
+  if (n_noise) TRY(project_noise(ctx, VT, N, deta, n_noise, &pe));
+  const int J = 4 * N + 5 * n_noise;
+  size_t bytes = (size_t)J * ctx->g.V * 12 * 16;
+  double* db = b;
+  if (mem == DLMA_MEM_HOST) TRY(workT(ctx, WS_SOL, bytes / 8, &db));
+  TRY(sources_range(ctx, 0, J, N, t_src, VT, deta, pe, db));
+  TRY(copy_out(ctx, b, db, bytes, mem));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return DLMA_OK;
 }
+
 extern "C" dlma_status dlma_project(dlma_ctx* ctx, int t, const double* V, int N, const double* psi, int nrhs,
                                     double* coeff, dlma_mem mem) {
-  (void)t; (void)V; (void)N; (void)psi; (void)nrhs; (void)coeff; (void)mem;
-  return set_err(ctx, DLMA_ERR_STATE, "not built yet");
+  if (!ctx) return DLMA_ERR_INVALID_ARG;
+  if (!V || !psi || !coeff || N < 1 || nrhs < 1 || t < -1 || t >= ctx->g.T)
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_project");
+  CU(cudaSetDevice(ctx->device));
+  const int n = 3 * ctx->g.Vs;
+  const int Tsel = t < 0 ? ctx->g.T : 1;
+  const double* dV;
+  TRY(copy_in(ctx, WS_PROJ_V, V, (size_t)Tsel * N * n * 16, mem, &dV));
+  const double* dpsi;
+  TRY(copy_in(ctx, WS_SRC, psi, (size_t)nrhs * ctx->g.V * 12 * 16, mem, &dpsi));
+  double2* VT;
+  // V: [T][N] (t = -1) or [N] vectors
+  TRY(transpose_V(ctx, dV, N, 1, Tsel, 0, N, &VT, WS_PROJ_PART));
+  size_t cbytes = (size_t)nrhs * Tsel * 4 * N * 16;
+  double* dc = coeff;
+  if (mem == DLMA_MEM_HOST) TRY(workT(ctx, WS_OUT, cbytes / 8, &dc));
+  TRY(project(ctx, VT, N, Tsel, dpsi, (size_t)ctx->g.V, t < 0 ? 0 : t, nrhs, (double2*)dc));
+  TRY(copy_out(ctx, coeff, dc, cbytes, mem));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return DLMA_OK;
 }
+
 extern "C" dlma_status dlma_contract(dlma_ctx* ctx, int t_src, int N, const double* V, int n_noise,
                                      const double* phi, double* C_dist, double* C_rest, double* C_mixed,
                                      dlma_mem mem) {
-  (void)t_src; (void)N; (void)V; (void)n_noise; (void)phi; (void)C_dist; (void)C_rest; (void)C_mixed; (void)mem;
-  return set_err(ctx, DLMA_ERR_STATE, "not built yet");
+  if (!ctx) return DLMA_ERR_INVALID_ARG;
+  if (!V || !phi || !C_dist || !C_rest || !C_mixed || N < 1 || n_noise < 0 || t_src < 0 || t_src >= ctx->g.T)
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_contract");
+  CU(cudaSetDevice(ctx->device));
+  const int T = ctx->g.T, n = 3 * ctx->g.Vs;
+  const int J = 4 * N + 5 * n_noise;
+  const double* dV;
+  TRY(copy_in(ctx, WS_PROJ_V, V, (size_t)T * N * n * 16, mem, &dV));
+  const double* dphi;
+  TRY(copy_in(ctx, WS_SRC, phi, (size_t)J * ctx->g.V * 12 * 16, mem, &dphi));
+  double2* VT;
+  TRY(transpose_V(ctx, dV, N, 1, T, 0, N, &VT, WS_PROJ_PART));
+  double2* coeff;
+  TRY(workT(ctx, WS_PROJ_C, (size_t)J * T * 4 * N, &coeff));
+  TRY(project(ctx, VT, N, T, dphi, (size_t)ctx->g.V, 0, J, coeff));
+  double2* M = nullptr;
+  if (n_noise) {
+    TRY(workT(ctx, WS_T1, (size_t)n_noise * 4 * T * 16, &M));
+    TRY(spin_inner(ctx, dphi + (size_t)4 * N * ctx->g.V * 24, n_noise, 0, M));
+  }
+  (void)t_src;
+  return finish_contract(ctx, N, n_noise, coeff, M, C_dist, C_rest, C_mixed);
 }
+
 extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* eta, double tol,
                                         dlma_prec inner, double* C_dist, double* C_rest, double* C_mixed,
                                         dlma_solve_info* info, dlma_mem mem) {
-  (void)t_src; (void)N; (void)n_noise; (void)eta; (void)tol; (void)inner; (void)C_dist; (void)C_rest; (void)C_mixed;
-  (void)info; (void)mem;
-  return set_err(ctx, DLMA_ERR_STATE, "not built yet");
+  if (!ctx) return DLMA_ERR_INVALID_ARG;
+  if (!ctx->have_gauge || !ctx->have_params) return set_err(ctx, DLMA_ERR_STATE, "gauge / params not set");
+  if (N < 1 || n_noise < 0 || (n_noise && !eta) || t_src < 0 || t_src >= ctx->g.T || !(tol > 0) || !C_dist ||
+      !C_rest || !C_mixed)
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_correlators");
+  if (ctx->eig_N != N) return set_err(ctx, DLMA_ERR_STATE, "no cached Laplacian modes for N = %d", N);
+  for (int t = 0; t < ctx->g.T; t++)
+    if (!ctx->eig_have[t]) return set_err(ctx, DLMA_ERR_STATE, "Laplacian modes of timeslice %d not computed", t);
+  CU(cudaSetDevice(ctx->device));
+  const int T = ctx->g.T, Vs = ctx->g.Vs, n = 3 * Vs;
+  const size_t V = ctx->g.V;
+  const int J = 4 * N + 5 * n_noise;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, ctx->stream));
+  const double* deta = nullptr;
+  if (n_noise) TRY(copy_in(ctx, WS_ETA + 0, eta, (size_t)n_noise * Vs * 12 * 16, mem, &deta));
+  // modes: all timeslices from the cache ([N][T] vectors) and the source timeslice
+  double2 *VT, *VTs;
+  TRY(transpose_V(ctx, (const double*)ctx->eig_V, 1, T, T, 0, N, &VT, WS_PROJ_PART));
+  TRY(transpose_V(ctx, (const double*)ctx->eig_V, 1, T, 1, t_src, N, &VTs, WS_PROJ_V));
+  double2* pe = nullptr;
+  if (n_noise) {
+    // copy eta out of the slot project_noise reuses
+    double2* etac;
+    TRY(workT(ctx, WS_CON + 0, (size_t)n_noise * Vs * 12 + 12 * T, &etac));
+    CU(cudaMemcpyAsync(etac, deta, (size_t)n_noise * Vs * 12 * 16, cudaMemcpyDeviceToDevice, ctx->stream));
+    deta = (const double*)etac;
+    TRY(project_noise(ctx, VTs, N, deta, n_noise, &pe));
+  }
+  double2* coeff;
+  TRY(workT(ctx, WS_PROJ_C, (size_t)J * T * 4 * N, &coeff));
+  double2* M = nullptr;
+  if (n_noise) TRY(workT(ctx, WS_T1, (size_t)n_noise * 4 * T * 16, &M));
+  // batch size: two full complex128 fields per rhs plus the solver's work space
+  size_t per_rhs = V * 12 * 16 * 2 + field_bytes_per_rhs(DLMA_FP64, ctx->g.Vh) * 7 +
+                   field_bytes_per_rhs(DLMA_FP32, ctx->g.Vh) * 8;
+  size_t freeb = 0, totb = 0;
+  cudaMemGetInfo(&freeb, &totb);
+  size_t budget = ctx->memcap ? ctx->memcap : (size_t)(0.8 * (double)freeb);
+  int nb = (int)std::max<size_t>(5, std::min<size_t>((size_t)J, budget / per_rhs));
+  nb = std::min(nb, J);
+  double *b, *x;
+  TRY(workT(ctx, WS_SRC, (size_t)nb * V * 24, &b));
+  TRY(workT(ctx, WS_SOL, (size_t)nb * V * 24, &x));
+  dlma_status worst = DLMA_OK;
+  // distillation rows in chunks of nb, then noise rows in whole groups of 5
+  int j0 = 0;
+  while (j0 < J) {
+    int cnt;
+    if (j0 < 4 * N) cnt = std::min(nb, 4 * N - j0);
+    else cnt = std::max(5, (nb / 5) * 5), cnt = std::min(cnt, J - j0);
+    TRY(sources_range(ctx, j0, cnt, N, t_src, VTs, deta, pe, b));
+    dlma_status s = solve_fields(ctx, b, x, cnt, tol, inner, info ? info + j0 : nullptr);
+    if (s != DLMA_OK && s != DLMA_ERR_NOT_CONVERGED) return s;
+    if (s != DLMA_OK) worst = s;
+    TRY(project(ctx, VT, N, T, x, V, 0, cnt, coeff + (size_t)j0 * T * 4 * N));
+    if (j0 >= 4 * N) {
+      int r0 = (j0 - 4 * N) / 5;
+      TRY(spin_inner(ctx, x, cnt / 5, 0, M + (size_t)r0 * 4 * T * 16));
+    }
+    j0 += cnt;
+  }
+  TRY(finish_contract(ctx, N, n_noise, coeff, M, C_dist, C_rest, C_mixed));
+  CU(cudaEventRecord(e1, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  ctx->timing[0] = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return worst;
 }

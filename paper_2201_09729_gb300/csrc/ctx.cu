@@ -28,8 +28,8 @@ dlma_status work(dlma_ctx* ctx, int slot, size_t bytes, void** out) {
       b.p = nullptr;
       b.bytes = 0;
     }
-    if (ctx->memcap && ctx->work_bytes + bytes > ctx->memcap)
-      return set_err(ctx, DLMA_ERR_OOM, "work space of %zu bytes exceeds the memory cap", bytes);
+    if (ctx->memcap && bytes > ctx->memcap)
+      return set_err(ctx, DLMA_ERR_OOM, "a work buffer of %zu bytes exceeds the memory cap", bytes);
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -290,12 +290,10 @@ __global__ void k_clover(Geom g, const double2* __restrict__ Ucan, SigmaBlocks s
   }
 }
 
-// sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu] in the chiral basis, split into its two 2x2 chirality blocks
-static SigmaBlocks sigma_blocks() {
-  typedef double c2[2];
-  // gamma matrices as 4x4 complex (re, im)
-  double G[4][4][4][2];
-  memset(G, 0, sizeof(G));
+// gamma_mu (mu = 0 time, 1..3 space) in the chiral basis as [mu][row][col][re, im]:
+// gamma_0 = -[[0, 1], [1, 0]], gamma_k = [[0, -i sigma_k], [i sigma_k, 0]]
+void gamma_matrices(double G[4][4][4][2]) {
+  memset(G, 0, sizeof(double) * 4 * 4 * 4 * 2);
   // gamma_0 = -[[0, 1], [1, 0]]
   for (int a = 0; a < 2; a++) { G[0][a][a + 2][0] = -1; G[0][a + 2][a][0] = -1; }
   // sigma_k (Pauli) entries
@@ -310,6 +308,12 @@ static SigmaBlocks sigma_blocks() {
         G[k + 1][a + 2][b][0] = -pi[k][a][b];
         G[k + 1][a + 2][b][1] = pr[k][a][b];
       }
+}
+
+// sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu] in the chiral basis, split into its two 2x2 chirality blocks
+static SigmaBlocks sigma_blocks() {
+  double G[4][4][4][2];
+  gamma_matrices(G);
   SigmaBlocks sb;
   int plane = 0;
   for (int mu = 0; mu < 4; mu++)
@@ -337,7 +341,6 @@ static SigmaBlocks sigma_blocks() {
           }
       plane++;
     }
-  (void)sizeof(c2);
   return sb;
 }
 

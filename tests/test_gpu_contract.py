@@ -1,0 +1,105 @@
+"""GPU parity of the distillation sources, the V^dag psi projections, the
+C_rest / C_mixed / C_dist contractions (Eqs. 2-4) and the whole per-source
+pipeline against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dirac, dlma
+from oracle import laplacian as lap
+from oracle import solve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dl():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2201_09729_gb300 as dl
+    return dl
+
+
+def _setup(dl, L, T, eps, kappa, csw, N, nn, seed):
+    U = synth.gauge_field(L, T, eps, seed)
+    m0 = 1 / (2 * kappa) - 4
+    ctx = dl.Context(L, T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    ctx.dlma_set_params(m0, csw)
+    eo = dirac.EvenOdd(U, L, T, m0, csw)
+    V_all = np.stack([lap.lap_modes(lap.timeslice_links(U, L, t), L, N)[1] for t in range(T)])
+    eta = synth.z2z2_noise(nn, L ** 3, seed + 1)
+    return ctx, eo, U, V_all, eta
+
+
+def _close(got, want, scale, tol):
+    return np.all(np.abs(got - want) <= tol * scale)
+
+
+def test_sources_and_projection(dl):
+    L, T, N, nn = 6, 4, 6, 3
+    ctx, eo, U, V_all, eta = _setup(dl, L, T, 0.2, 0.12, 1.0, N, nn, 301)
+    tp = 1
+    b = ctx.dlma_make_sources(tp, np.ascontiguousarray(V_all[tp]), eta)
+    want = np.concatenate([dlma.distillation_sources(V_all[tp], L, T, tp),
+                           dlma.noise_sources(eta, V_all[tp], L, T, tp).reshape(5 * nn, L ** 3 * T, 4, 3)])
+    assert np.abs(b - want).max() < 1e-14
+    psi = synth.gaussian_spinors(5, L ** 3 * T, 302)
+    c_all = ctx.dlma_project(-1, np.ascontiguousarray(V_all), psi)          # [5, T, 4, N]
+    for t in range(T):
+        w = dlma.coeffs(V_all[t], dlma.timeslice(psi, L, t))               # [5, k, alpha]
+        assert np.abs(c_all[:, t] - np.transpose(w, (0, 2, 1))).max() < 1e-12
+    c1 = ctx.dlma_project(2, np.ascontiguousarray(V_all[2]), psi)
+    assert np.abs(c1[:, 0] - c_all[:, 2]).max() < 1e-13
+
+
+def test_contract_vs_oracle(dl):
+    L, T, N, nn = 4, 8, 5, 3
+    ctx, eo, U, V_all, eta = _setup(dl, L, T, 0.2, 0.12, 1.0, N, nn, 303)
+    lu = solve.lu_solver(eo)
+    r = dlma.dlma_correlators(lu, V_all, eta, L, T, 0)
+    phi = np.concatenate([r["phi_dist"], r["phi_noise"].reshape(5 * nn, L ** 3 * T, 4, 3)])
+    got = ctx.dlma_contract(0, np.ascontiguousarray(V_all), np.ascontiguousarray(phi), nn)
+    scale = np.abs(r["C"]).max(axis=1, keepdims=True)
+    for key in ("C_dist", "C_rest", "C_mixed"):
+        assert _close(got[key], r[key], scale, 1e-12), key
+
+
+@pytest.mark.parametrize("prec,tol,ctol", [("FP64", 1e-12, 1e-10), ("FP32", 1e-10, 1e-8), ("FP16S", 1e-10, 1e-8)])
+def test_pipeline_plain_workload(dl, prec, tol, ctol):
+    # the 4^3 x 8 workload end to end: GPU modes, sources, solves, contractions
+    wl = synth.WORKLOADS["plain_4c8"]
+    U, eta = synth.workload_inputs(wl)
+    ctx = dl.Context(wl.L, wl.T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    ctx.dlma_set_params(wl.m0, wl.csw)
+    lam, _ = ctx.dlma_laplacian_eigs(-1, wl.n_modes, 1e-13, want_vecs=False)
+    res = ctx.dlma_correlators(0, wl.n_modes, eta[0], tol, getattr(dl, prec))
+    assert all(i["converged"] and i["true_resid"] <= tol for i in res["info"])
+    assert len(res["info"]) == 4 * wl.n_modes + 5 * wl.n_noise
+    eo = dirac.EvenOdd(U, wl.L, wl.T, wl.m0, wl.csw)
+    V_all = np.stack([lap.lap_modes(lap.timeslice_links(U, wl.L, t), wl.L, wl.n_modes)[1] for t in range(wl.T)])
+    ref = dlma.dlma_correlators(solve.lu_solver(eo), V_all, eta[0], wl.L, wl.T, 0)
+    scale = np.abs(ref["C"]).max(axis=1, keepdims=True)
+    for key in ("C_dist", "C_rest", "C_mixed", "C"):
+        err = np.abs(res[key] - ref[key]).max(axis=1) / scale[:, 0]
+        assert np.all(err <= ctol), (key, err)
+    # pseudoscalar C_dist is tr[tau tau^dag]: real and positive
+    assert np.all(res["C_dist"][0].real > 0)
+
+
+def test_pipeline_ragged_batches_with_memory_cap(dl):
+    # a memory cap forces several solve batches; results must equal the uncapped run
+    L, T, N, nn = 6, 8, 6, 3
+    U = synth.gauge_field(L, T, 0.2, 305)
+    ctx = dl.Context(L, T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    ctx.dlma_set_params(1 / 0.24 - 4, 1.0)
+    ctx.dlma_laplacian_eigs(-1, N, 1e-12, want_vecs=False)
+    eta = synth.z2z2_noise(nn, L ** 3, 306)
+    full = ctx.dlma_correlators(0, N, eta, 1e-11, dl.FP64)
+    V = L ** 3 * T
+    ctx.dlma_set_memory_cap(int(7 * V * 12 * 16 * 6))
+    capped = ctx.dlma_correlators(0, N, eta, 1e-11, dl.FP64)
+    for key in ("C_dist", "C_rest", "C_mixed"):
+        assert np.abs(capped[key] - full[key]).max() <= 1e-9 * np.abs(full["C"]).max()

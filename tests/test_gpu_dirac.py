@@ -91,8 +91,9 @@ def test_solve_fp64_plain_workload_vs_lu(dl):
 
 @pytest.mark.parametrize("prec", ["FP32", "FP16S"])
 def test_mixed_precision_solve_ragged_batch(dl, prec):
-    # 7 right-hand sides (ragged against the 4-rhs block), one of them zero
-    L, T = 6, 8
+    # 7 right-hand sides (ragged against the 4-rhs block), one of them zero;
+    # V/2 = 432 sites: 6.75 tiles of 64
+    L, T = 6, 4
     ctx, eo = _ctx(dl, L, T, 0.2, 0.0816, 1.0, 108)
     b = synth.gaussian_spinors(7, L ** 3 * T, 109)
     b[3] = 0

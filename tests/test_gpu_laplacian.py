@@ -1,0 +1,88 @@
+"""GPU parity of the spatial Laplacian (Eq. 1) and of its low modes against
+the FP64 oracle (dense eigh / ARPACK), through the C ABI."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import laplacian as lap
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dl():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2201_09729_gb300 as dl
+    return dl
+
+
+def _proj(Vm):
+    return np.einsum("kmc,knd->mcnd", Vm, np.conj(Vm))
+
+
+def test_apply_laplacian(dl):
+    L, T = 6, 4
+    U = synth.gauge_field(L, T, 0.3, 201)
+    ctx = dl.Context(L, T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    v = synth.gaussian_spinors(2, L ** 3 * T, 202)[:, :, 0, :].copy()      # [2, V, 3]
+    got = ctx.dlma_apply_laplacian(np.ascontiguousarray(v))
+    for t in range(T):
+        sl = slice(t * L ** 3, (t + 1) * L ** 3)
+        want = lap.lap_apply(lap.timeslice_links(U, L, t), L, v[:, sl])
+        assert np.abs(got[:, sl] - want).max() < 1e-13 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("L,T,N,t", [(4, 4, 8, 2), (6, 2, 20, -1), (8, 4, 16, -1)])
+def test_eigs_vs_dense(dl, L, T, N, t):
+    U = synth.gauge_field(L, T, 0.2, 203 + L)
+    ctx = dl.Context(L, T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    lam, V = ctx.dlma_laplacian_eigs(t, N, 1e-12)
+    ts = [t] if t >= 0 else list(range(T))
+    lam = lam.reshape(len(ts), N)
+    V = V.reshape(len(ts), N, L ** 3, 3)
+    for i, tt in enumerate(ts):
+        w, Z = lap.lap_modes(lap.timeslice_links(U, L, tt), L, N + 1)
+        assert w[N] - w[N - 1] > 1e-6            # a gap at the cut: the projector is unique
+        assert np.all(np.abs(lam[i] - w[:N]) <= 1e-9 * np.maximum(np.abs(w[:N]), 1.0))
+        assert np.linalg.norm((_proj(V[i]) - _proj(Z[:N])).ravel()) <= 1e-8
+        gram = np.einsum("kmc,lmc->kl", np.conj(V[i]), V[i])
+        assert np.abs(gram - np.eye(N)).max() < 1e-12
+
+
+def test_eigs_free_field_degenerate_clusters(dl):
+    # free field on 4^3: -lap eigenvalues 0 (x3), 2 (x18), ...; cuts at cluster boundaries
+    L, T = 4, 2
+    ctx = dl.Context(L, T, 0, 0)
+    ctx.dlma_set_gauge(synth.unit_gauge(L, T))
+    for N in (3, 21):
+        lam, V = ctx.dlma_laplacian_eigs(-1, N, 1e-12)
+        want = np.array([0.0] * 3 + [2.0] * 18)[:N]
+        assert np.abs(lam - want[None]).max() < 1e-11
+        Z = lap.lap_modes(lap.timeslice_links(synth.unit_gauge(L, T), L, 0), L, N)[1]
+        for t in range(T):
+            assert np.linalg.norm((_proj(V[t]) - _proj(Z)).ravel()) <= 1e-8
+
+
+def test_eigs_precision_workload_sampled(dl):
+    # 16^3 x 32, N = 32 on every timeslice; the oracle checks sampled timeslices
+    wl = synth.WORKLOADS["precision_16c32"]
+    U, _ = synth.workload_inputs(wl)
+    ctx = dl.Context(wl.L, wl.T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    lam, V = ctx.dlma_laplacian_eigs(-1, wl.n_modes, 1e-10)
+    assert lam.shape == (wl.T, wl.n_modes)
+    for t in (0, 17):
+        Ut = lap.timeslice_links(U, wl.L, t)
+        w, Z = lap.lap_modes(Ut, wl.L, wl.n_modes + 1)
+        assert np.all(np.abs(lam[t] - w[:-1]) <= 1e-9 * np.maximum(np.abs(w[:-1]), 1.0))
+        if w[-1] - w[-2] > 1e-4:
+            assert np.linalg.norm((_proj(V[t]) - _proj(Z[:-1])).ravel()) <= 1e-8
+    # every timeslice: residuals by the oracle's operator for a sample of modes
+    for t in range(0, wl.T, 5):
+        Ut = lap.timeslice_links(U, wl.L, t)
+        for k in (0, wl.n_modes // 2, wl.n_modes - 1):
+            r = -lap.lap_apply(Ut, wl.L, V[t, k]) - lam[t, k] * V[t, k]
+            assert np.linalg.norm(r) <= 1e-10 * max(1.0, lam[t, k])
