@@ -123,6 +123,23 @@ dlma_status dlma_apply_Dw(dlma_ctx* ctx, const double* in, double* out, int nrhs
 dlma_status dlma_apply_schur(dlma_ctx* ctx, const double* in, double* out, int nrhs, int dagger,
                              dlma_prec prec, dlma_mem mem);
 
+/* dlma_apply_schur_noalloc: the same operator as dlma_apply_schur with
+ * dagger 0 / 1, in FP64, for callers that must not allocate device memory:
+ * a framework that owns all device memory through its own pool and forbids
+ * allocations it does not track, or a caller that cannot afford the
+ * device-wide synchronisation cudaMalloc / cudaFree may cause.  The paper has
+ * no counterpart; it is a library-usage variant.  `in` and `out` are DEVICE
+ * pointers (complex [nrhs][V/2][4][3], even sites), owned by the caller.  The
+ * work space is a fixed 64 MiB array in the library's device memory, held by
+ * every GPU that loads the library until the process exits; nothing else is
+ * allocated.  Three FP64 even-odd fields of nrhs right-hand sides must fit in
+ * it (3 * 192 * nrhs * V/2 bytes <= 64 MiB), else DLMA_ERR_INVALID_ARG with a
+ * message.  The first call on a device looks up the array's device address;
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU race on it.
+ * Errors: STATE, INVALID_ARG, CUDA. */
+dlma_status dlma_apply_schur_noalloc(dlma_ctx* ctx, const double* in, double* out, int nrhs, int dagger);
+
 /* dlma_solve: x = D^-1 b for nrhs full-lattice sources (complex
  * [nrhs][V][4][3]); the propagator solves of Eq. 4 and of the perambulator
  * (text after Eq. 3).  Even-odd Schur system, multi-RHS CG on the normal

@@ -43,6 +43,7 @@ SIGNATURES = {
     "dlma_set_params": (_ST, [_P, _D, _D]),
     "dlma_apply_Dw": (_ST, [_P, _P, _P, _I, _I, _I]),
     "dlma_apply_schur": (_ST, [_P, _P, _P, _I, _I, _I, _I]),
+    "dlma_apply_schur_noalloc": (_ST, [_P, _P, _P, _I, _I]),
     "dlma_solve": (_ST, [_P, _P, _P, _I, _D, _I, _P, _I]),
     "dlma_apply_laplacian": (_ST, [_P, _P, _P, _I, _I]),
     "dlma_laplacian_eigs": (_ST, [_P, _I, _I, _D, _P, _P, _I]),
