@@ -235,11 +235,13 @@ def main():
     ctx.dlma_set_gauge(U_d)
     ctx.dlma_set_params(wl.m0, wl.csw)
 
-    phase = {"eigs_ms": [], "corr_ms": []}
+    phase = {"eigs_ms": [], "corr_ms": [], "eig_iters": []}
 
     def step():
         ctx.dlma_laplacian_eigs(-1, N, 1e-10, device_out=True, want_vecs=False)
-        phase["eigs_ms"].append(ctx.dlma_last_timing()[0])
+        tm = ctx.dlma_last_timing()
+        phase["eigs_ms"].append(tm[0])
+        phase["eig_iters"].append([int(tm[1]), int(tm[2])])
         r = ctx.dlma_correlators(0, N, eta_d, wl.tol, inner)
         phase["corr_ms"].append(ctx.dlma_last_timing()[0])
         return r
@@ -247,7 +249,7 @@ def main():
     for _ in range(args.warmup):
         res = step()
     assert all(i["converged"] for i in res["info"]), "a solve did not converge"
-    phase = {"eigs_ms": [], "corr_ms": []}
+    phase = {"eigs_ms": [], "corr_ms": [], "eig_iters": []}
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -336,6 +338,7 @@ def main():
                      "peak_source": f"{peak_kind} HBM copy bandwidth"},
         "clocks": clocks,
         "breakdown": {"eigs_ms": statistics.mean(phase["eigs_ms"]), "correlators_ms": statistics.mean(phase["corr_ms"]),
+                      "eig_iterations_fp32_fp64": phase["eig_iters"][-1],
                       "solves_per_s_correlator_phase": corr_solve_sps,
                       "fp64_single_rhs_solves_per_s": fp64_sps,
                       "speedup_mixed_batched_vs_fp64_single": corr_solve_sps / fp64_sps,

@@ -91,6 +91,8 @@ struct dlma_ctx {
   uint64_t memcap = 0;
   uint64_t work_bytes = 0;      // bytes currently held in work buffers
   double timing[3] = {0, 0, 0};
+  // stencil block shape (sites x right-hand sides) per precision, chosen by autotune_hop
+  int hop_sx[3] = {64, 64, 64}, hop_sy[3] = {4, 4, 4}, hop_tuned[3] = {0, 0, 0};
 
   bool have_gauge = false, have_params = false;
   double m0 = 0, csw = 0;
@@ -112,6 +114,11 @@ struct dlma_ctx {
   uint4* C16 = nullptr;     // [2][9][Vh]
   uint4* Ci16 = nullptr;
   int* flag = nullptr;      // device status flags [16]
+  // neighbour table of the stencil: for output parity p, int4 words w = 0, 1 hold
+  // directions 4w .. 4w+3 (direction 2 mu + 0 forward / 1 backward): the compressed
+  // index of the neighbour in parity 1 - p; bit 31 set when the hop picks up the
+  // antiperiodic time phase.  Layout int4 [2][2][V/2].
+  int4* nbr_tab = nullptr;
 
   // cached Laplacian modes (all timeslices)
   int eig_N = 0;
@@ -222,6 +229,7 @@ int hop_grid_x(dlma_ctx* ctx, int prec);
 // Schur operator on even fields: out = Dhat in (dagger: gamma5 Dhat gamma5), tmp: odd work field
 dlma_status schur_apply(dlma_ctx* ctx, const Field& in, Field& tmp, Field& out, int dagger,
                         const int* active, double* norm_part);
+dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, Field& out);
 
 void gamma_matrices(double G[4][4][4][2]);
 dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol,

@@ -344,24 +344,45 @@ static SigmaBlocks sigma_blocks() {
   return sb;
 }
 
-__global__ void k_index_tables(Geom g, int* eo_index, int* nbr) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+// the stencil's neighbour table (see dlma_ctx::nbr_tab)
+__global__ void k_build_nbr(Geom g, int bc_t, int4* tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.Vh) return;
+  for (int p = 0; p < 2; p++) {
+    const Coord c = eo_coords(g, p, i);
+    int v[8];
+    for (int mu = 0; mu < 4; mu++) {
+      v[2 * mu] = nbr_lex(g, c, mu, +1) >> 1;
+      v[2 * mu + 1] = nbr_lex(g, c, mu, -1) >> 1;
+    }
+    if (bc_t) {
+      if (c.t == g.T - 1) v[0] |= (int)0x80000000u;
+      if (c.t == 0) v[1] |= (int)0x80000000u;
+    }
+    tab[((size_t)p * 2 + 0) * g.Vh + i] = make_int4(v[0], v[1], v[2], v[3]);
+    tab[((size_t)p * 2 + 1) * g.Vh + i] = make_int4(v[4], v[5], v[6], v[7]);
+  }
+}
+
+// dlma_index_tables: the compressed index of every site and the stencil's own
+// neighbour table with the phase bit removed
+__global__ void k_index_tables(Geom g, const int4* tab, int* eo_index, int* nbr) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < g.V) eo_index[s] = s >> 1;
   if (s < g.Vh) {
-    for (int p = 0; p < 2; p++) {
-      Coord c = eo_coords(g, p, s);
-      for (int mu = 0; mu < 4; mu++) {
-        nbr[((size_t)p * 8 + 2 * mu) * g.Vh + s] = nbr_lex(g, c, mu, +1) >> 1;
-        nbr[((size_t)p * 8 + 2 * mu + 1) * g.Vh + s] = nbr_lex(g, c, mu, -1) >> 1;
+    for (int p = 0; p < 2; p++)
+      for (int w = 0; w < 2; w++) {
+        const int4 q = tab[((size_t)p * 2 + w) * g.Vh + s];
+        const int v[4] = {q.x, q.y, q.z, q.w};
+        for (int k = 0; k < 4; k++) nbr[((size_t)p * 8 + 4 * w + k) * g.Vh + s] = v[k] & 0x7fffffff;
       }
-    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // C ABI
 static void free_all(dlma_ctx* ctx) {
-  void* ptrs[] = {ctx->Ucan, ctx->U64, ctx->U32, ctx->U16a, ctx->U16b, ctx->U3, ctx->U3f, ctx->C64, ctx->Ci64,
+  void* ptrs[] = {ctx->nbr_tab, ctx->Ucan, ctx->U64, ctx->U32, ctx->U16a, ctx->U16b, ctx->U3, ctx->U3f, ctx->C64, ctx->Ci64,
                   ctx->C32, ctx->Ci32, ctx->C16, ctx->Ci16, ctx->flag, ctx->eig_V};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -417,6 +438,7 @@ extern "C" dlma_status dlma_create(const dlma_lattice* lat, int device, void* cu
             cudaMalloc(&ctx->C16, 2 * 9 * Vh * sizeof(uint4)) == cudaSuccess &&
             cudaMalloc(&ctx->Ci16, 2 * 9 * Vh * sizeof(uint4)) == cudaSuccess &&
             cudaMalloc(&ctx->flag, 16 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&ctx->nbr_tab, 4 * Vh * sizeof(int4)) == cudaSuccess &&
             cudaMallocHost(&ctx->pinned, 1 << 20) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -424,6 +446,13 @@ extern "C" dlma_status dlma_create(const dlma_lattice* lat, int device, void* cu
     delete ctx;
     return DLMA_ERR_OOM;
   }
+  k_build_nbr<<<(ctx->g.Vh + 255) / 256, 256, 0, ctx->stream>>>(ctx->g, ctx->bc_t, ctx->nbr_tab);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    free_all(ctx);
+    delete ctx;
+    return DLMA_ERR_CUDA;
+  }
+  ctx->launches++;
   *out = ctx;
   return DLMA_OK;
 }
@@ -511,7 +540,7 @@ extern "C" dlma_status dlma_index_tables(dlma_ctx* ctx, int32_t* eo_index, int32
   int *d_eo, *d_nbr;
   TRY(workT(ctx, WS_T0, (size_t)ctx->g.V, &d_eo));
   TRY(workT(ctx, WS_T1, (size_t)16 * ctx->g.Vh, &d_nbr));
-  k_index_tables<<<(ctx->g.V + 255) / 256, 256, 0, ctx->stream>>>(ctx->g, d_eo, d_nbr);
+  k_index_tables<<<(ctx->g.V + 255) / 256, 256, 0, ctx->stream>>>(ctx->g, ctx->nbr_tab, d_eo, d_nbr);
   CHECK_LAUNCH();
   CU(cudaMemcpyAsync(eo_index, d_eo, sizeof(int) * ctx->g.V, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaMemcpyAsync(nbr, d_nbr, sizeof(int) * 16 * (size_t)ctx->g.Vh, cudaMemcpyDeviceToHost, ctx->stream));

@@ -133,6 +133,7 @@ struct HopArgs {
   double s;
   double* norm_part;
   const int* active;
+  const int4* nbr;    // neighbour table (dlma_ctx::nbr_tab)
 };
 
 template <class R>
@@ -158,10 +159,13 @@ __device__ __forceinline__ void su3_dag_mul(const Cx<R> U[3][3], const Cx<R> h[3
 }
 
 template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM>
-__global__ void __launch_bounds__(256) k_hop(HopArgs a) {
+__global__ void __launch_bounds__(256, P == DLMA_FP64 ? 2 : 3) k_hop(HopArgs a) {
   typedef typename PT<P>::R R;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  // grid x runs over right-hand-side groups (fast), grid y over site tiles: all
+  // right-hand sides of a site tile run back to back, so its links and clover
+  // come from DRAM once and from L2 afterwards
+  const int i = blockIdx.y * blockDim.x + threadIdx.x;
+  const int j = blockIdx.x * blockDim.y + threadIdx.y;
   const Geom g = a.g;
   bool valid = i < g.Vh && j < a.nrhs;
   if (valid && a.active) valid = a.active[j] != 0;
@@ -173,7 +177,9 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a) {
 #pragma unroll
       for (int c = 0; c < 3; c++) res.c[s][c] = cx<R>(0, 0);
     if (HOP) {
-      const Coord co = eo_coords(g, a.p_out, i);
+      const int4 q0 = __ldg(a.nbr + ((size_t)a.p_out * 2 + 0) * g.Vh + i);
+      const int4 q1 = __ldg(a.nbr + ((size_t)a.p_out * 2 + 1) * g.Vh + i);
+      const int nb8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
       const char* inb = (const char*)a.in;
       const void* in_j = inb + (size_t)j * a.in_stride;
       const float* sc_j = a.in_scale ? a.in_scale + (size_t)j * g.Vh : nullptr;
@@ -181,8 +187,8 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a) {
       for (int mu = 0; mu < 4; mu++) {
 #pragma unroll
         for (int dir = 0; dir < 2; dir++) {
-          const int sgn = dir == 0 ? +1 : -1;
-          const int n = nbr_lex(g, co, mu, sgn) >> 1;
+          const int raw = nb8[2 * mu + dir];
+          const int n = raw & 0x7fffffff;
           Spinor<R> ps = load_spinor<P>(in_j, sc_j, g.Vh, n);
           if (G5IN) {
 #pragma unroll
@@ -191,11 +197,7 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a) {
           Cx<R> U[3][3];
           // forward: U_mu(x) at this site; backward: U_mu(x - mu) at the neighbour
           load_link<P>(a.Ua, a.Ub, dir == 0 ? a.p_out : 1 - a.p_out, mu, dir == 0 ? i : n, g.Vh, U);
-          R ph = 1;
-          if (mu == 0 && a.bc_t) {
-            if (dir == 0 && co.t == g.T - 1) ph = -1;
-            if (dir == 1 && co.t == 0) ph = -1;
-          }
+          const R ph = raw < 0 ? (R)-1 : (R)1;    // antiperiodic time phase (bit 31)
           Cx<R> h0[3], h1[3], w0[3], w1[3];
 #pragma unroll
           for (int c = 0; c < 3; c++) {
@@ -273,22 +275,23 @@ __global__ void __launch_bounds__(256) k_hop(HopArgs a) {
     if (threadIdx.x == 0 && j < a.nrhs) {
       double t = 0;
       for (int w = 0; w < nwx; w++) t += red[threadIdx.y * nwx + w];
-      a.norm_part[(size_t)j * gridDim.x + blockIdx.x] = t;
+      a.norm_part[(size_t)j * gridDim.y + blockIdx.y] = t;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 // host dispatch
-static inline void hop_block(int prec, int& sx, int& sy) {
-  (void)prec;
-  sx = 64;
-  sy = 4;
+// block shape (sites x right-hand sides) per precision, set by autotune_hop
+static inline void hop_block(dlma_ctx* ctx, int prec, int& sx, int& sy) {
+  sx = ctx->hop_sx[prec];
+  sy = ctx->hop_sy[prec];
 }
 
+// number of site tiles of a hop launch (= partial sums per right-hand side)
 int hop_grid_x(dlma_ctx* ctx, int prec) {
   int sx, sy;
-  hop_block(prec, sx, sy);
+  hop_block(ctx, prec, sx, sy);
   return (ctx->g.Vh + sx - 1) / sx;
 }
 
@@ -338,6 +341,7 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   a.s = op.s;
   a.norm_part = op.norm_part;
   a.active = op.active;
+  a.nbr = ctx->nbr_tab;
   const size_t Vh = ctx->g.Vh;
   const int p = op.p_out;
   const void* Kown = nullptr;
@@ -358,14 +362,47 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   a.Kown = Kown;
   a.Kout = Kout;
   int sx, sy;
-  hop_block(P, sx, sy);
+  hop_block(ctx, P, sx, sy);
   dim3 blk(sx, sy);
-  dim3 grid((ctx->g.Vh + sx - 1) / sx, (out.nrhs + sy - 1) / sy);
-  if (nblocks_out) *nblocks_out = grid.x;
+  dim3 grid((out.nrhs + sy - 1) / sy, (ctx->g.Vh + sx - 1) / sx);
+  if (nblocks_out) *nblocks_out = grid.y;
   if (P == DLMA_FP64) dispatch<DLMA_FP64>(op, grid, blk, ctx->stream, a);
   else if (P == DLMA_FP32) dispatch<DLMA_FP32>(op, grid, blk, ctx->stream, a);
   else dispatch<DLMA_FP16S>(op, grid, blk, ctx->stream, a);
   CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+// Autotuner: time the Schur operator (both hop launches) on the caller's own
+// fields for each candidate block shape and keep the fastest for this precision.
+dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, Field& out) {
+  if (ctx->hop_tuned[prec]) return DLMA_OK;
+  static const int cand[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}, {32, 2}};
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bx = ctx->hop_sx[prec], by = ctx->hop_sy[prec];
+  for (const auto& c : cand) {
+    ctx->hop_sx[prec] = c[0];
+    ctx->hop_sy[prec] = c[1];
+    float tot = 0;
+    for (int r = 0; r < 3; r++) {
+      CU(cudaEventRecord(e0, ctx->stream));
+      TRY(schur_apply(ctx, in, tmp, out, 0, nullptr, nullptr));
+      CU(cudaEventRecord(e1, ctx->stream));
+      CU(cudaEventSynchronize(e1));
+      float ms = 0;
+      CU(cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0) tot += ms;
+    }
+    if (tot < best) { best = tot; bx = c[0]; by = c[1]; }
+  }
+  ctx->hop_sx[prec] = bx;
+  ctx->hop_sy[prec] = by;
+  ctx->hop_tuned[prec] = 1;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return DLMA_OK;
 }
 
@@ -520,6 +557,7 @@ extern "C" dlma_status dlma_apply_schur(dlma_ctx* ctx, const double* in, double*
   TRY(field_alloc(ctx, WS_T1, prec, nrhs, &tmp));
   TRY(field_alloc(ctx, WS_T2, prec, nrhs, &res));
   TRY(pack_parity(ctx, din, 0, 0, fe));
+  TRY(autotune_hop(ctx, prec, fe, tmp, res));
   EvTimer ev;
   CU(cudaEventCreate(&ev.a));
   CU(cudaEventCreate(&ev.b));

@@ -3,116 +3,157 @@
 //
 //   (lap v)(m, t) = -6 v(m) + sum_{j=1..3} [U_j(m,t) v(m+j) + U_j(m-j,t)^dag v(m-j)]
 //
-// The modes are the N lowest eigenpairs of A = -lap(t) (spectrum in [0, 12]),
-// for every timeslice at once: a Chebyshev-filtered subspace iteration.  Each
-// iteration filters an m-column block (m = N + buffer) with a degree-d
-// Chebyshev polynomial of A that damps [cut, 12], then orthonormalises and
-// diagonalises the filtered block (Rayleigh-Ritz) per timeslice:
+// The modes are the N lowest eigenpairs of A = -lap(t) (spectrum in [0, 12]) on
+// every timeslice at once, by Chebyshev-filtered subspace iteration on a block
+// of m = N + buffer vectors per timeslice.  Each iteration filters the block
+// with a degree-d Chebyshev polynomial of A that damps [cut, 12] and then
+// diagonalises it per timeslice (Rayleigh-Ritz):
 //   G = Y^dag Y, H = Y^dag (A Y)  ->  G = Q diag(g) Q^dag, S = Q g^-1/2,
 //   S^dag H S = Z diag(theta) Z^dag,  X <- Y S Z,  A X <- (A Y) S Z,
-// all in FP64 (the small m x m eigenproblems by parallel cyclic Jacobi, one
-// CTA per timeslice).  Stops when every wanted pair has
-// ||A x - theta x|| <= tol * max(theta, 1).
-// Block layout: column j of timeslice t (of a batch of Tn timeslices starting
-// at t0) is the colour field [Vs][3] at offset (j * Tn + t) * 3 Vs.
+// with the small m x m eigenproblems solved by parallel cyclic Jacobi in the
+// block's precision (smalleig.cuh; one CTA per timeslice).
+//
+// Precision: phase A runs the whole iteration in FP32 until the residuals reach
+// ~1e-5.  Phase B keeps X, A X and the Rayleigh-Ritz in FP64 but still filters
+// in FP32, on the residual: with R = A X - X Theta and the filter's scalar
+// recurrence s_k(theta), p_k(A) X = X s_k(Theta) + E_k where
+//   E_{k+1} = a_k A E_k + b_k E_k + c_k E_{k-1} + a_k R s_k(Theta),  E_0 = 0,
+// so the FP32 rounding only touches the (small) E, and Y = X s_d + E_d is formed
+// in FP64.  Stops when every wanted pair has ||A x - theta x|| <= tol max(theta, 1).
+//
+// Block layout (row-major per timeslice): element (t, row r = 3 site + colour,
+// column j) of a batch of Tn timeslices at (t * 3 Vs + r) * m + j, so a warp
+// reads consecutive columns of one site (coalesced) and shares its links.
 #include "common.cuh"
+#include "smalleig.cuh"
 #include <algorithm>
 #include <math.h>
 
 namespace {
 
-// --------------------------------------------------------------------------
-// fused stencil: out = alpha_t (A in) + beta_t in + gamma_t prev, A = -lap
-__global__ void __launch_bounds__(128) k_lap_fused(Geom g, int t0, int Tn, const double2* __restrict__ U3,
-                                                   const double2* __restrict__ in, const double2* __restrict__ prev,
-                                                   double2* __restrict__ out, int nvec, const double* __restrict__ coef) {
-  const int sl = blockIdx.x * blockDim.x + threadIdx.x;     // site within the batch
-  const int j = blockIdx.y;
-  if (sl >= Tn * g.Vs || j >= nvec) return;
+template <class R> struct LinkT;
+template <> struct LinkT<double> { typedef double2 T; };
+template <> struct LinkT<float> { typedef float4 T; };
+
+__device__ __forceinline__ void load_link3(const double2* __restrict__ U, int k, size_t s, size_t V, Cx<double> u[3][3]) {
+#pragma unroll
+  for (int q = 0; q < 9; q++) {
+    double2 e = __ldg(U + ((size_t)k * 9 + q) * V + s);
+    u[q / 3][q % 3] = cx<double>(e.x, e.y);
+  }
+}
+__device__ __forceinline__ void load_link3(const float4* __restrict__ U, int k, size_t s, size_t V, Cx<float> u[3][3]) {
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    float4 e = __ldg(U + ((size_t)k * 3 + q) * V + s);
+    u[(2 * q) / 3][(2 * q) % 3] = cx<float>(e.x, e.y);
+    u[(2 * q + 1) / 3][(2 * q + 1) % 3] = cx<float>(e.z, e.w);
+  }
+  u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+  u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+  u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+}
+
+// out = alpha_t (A in) + beta_t in + gamma_t prev + alpha_t s[t][j] rin,  A = 6 - hopping = -lap
+// (in == nullptr: the stencil and beta terms vanish; prev / rin may be nullptr)
+template <class R>
+__global__ void __launch_bounds__(256) k_lap(Geom g, int t0, int Tn, int m, const typename LinkT<R>::T* __restrict__ U,
+                                             const Cx<R>* __restrict__ in, const Cx<R>* __restrict__ prev,
+                                             const Cx<float>* __restrict__ rin, const double* __restrict__ scol,
+                                             Cx<R>* __restrict__ out, const double* __restrict__ coef) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t total = (size_t)Tn * g.Vs * m;
+  if (e >= total) return;
+  const int j = e % m;
+  const size_t sl = e / m;
   const int tl = sl / g.Vs;
-  const int m = sl - tl * g.Vs;
-  const int x = m % g.L, y = (m / g.L) % g.L, z = m / (g.L * g.L);
-  const size_t s = (size_t)(t0 + tl) * g.Vs + m;            // global site for links
-  const size_t col = ((size_t)j * Tn + tl) * g.Vs * 3;
-  const double2* v = in + col;
-  const double alpha = coef[3 * tl], beta = coef[3 * tl + 1], gamma = coef[3 * tl + 2];
-  Cx<double> own[3], acc[3];
+  const int ms = sl - (size_t)tl * g.Vs;
+  const R alpha = (R)coef[3 * tl], beta = (R)coef[3 * tl + 1], gamma = (R)coef[3 * tl + 2];
+  const size_t rowbase = (size_t)tl * g.Vs;
+  Cx<R> res[3];
 #pragma unroll
-  for (int a = 0; a < 3; a++) {
-    double2 e = v[(size_t)m * 3 + a];
-    own[a] = cx<double>(e.x, e.y);
-    acc[a] = cx<double>(6.0 * e.x, 6.0 * e.y);       // A = 6 - hopping
-  }
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    int xf = x, yf = y, zf = z, xb = x, yb = y, zb = z;
-    if (k == 0) { xf = x + 1 == g.L ? 0 : x + 1; xb = x == 0 ? g.L - 1 : x - 1; }
-    else if (k == 1) { yf = y + 1 == g.L ? 0 : y + 1; yb = y == 0 ? g.L - 1 : y - 1; }
-    else { zf = z + 1 == g.L ? 0 : z + 1; zb = z == 0 ? g.L - 1 : z - 1; }
-    const int mf = xf + g.L * (yf + g.L * zf), mb = xb + g.L * (yb + g.L * zb);
-    const size_t sb = (size_t)(t0 + tl) * g.Vs + mb;
-    Cx<double> vf[3], vb[3];
+  for (int a = 0; a < 3; a++) res[a] = cx<R>(0, 0);
+  if (in) {
+    const int x = ms % g.L, y = (ms / g.L) % g.L, z = ms / (g.L * g.L);
+    const size_t s = (size_t)(t0 + tl) * g.Vs + ms;
+    Cx<R> own[3], acc[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      double2 e = v[(size_t)mf * 3 + a];
-      vf[a] = cx<double>(e.x, e.y);
-      e = v[(size_t)mb * 3 + a];
-      vb[a] = cx<double>(e.x, e.y);
+      own[a] = in[((rowbase + ms) * 3 + a) * m + j];
+      acc[a] = (R)6 * own[a];
     }
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-      Cx<double> h = cx<double>(0, 0);
+    for (int k = 0; k < 3; k++) {
+      int xf = x, yf = y, zf = z, xb = x, yb = y, zb = z;
+      if (k == 0) { xf = x + 1 == g.L ? 0 : x + 1; xb = x == 0 ? g.L - 1 : x - 1; }
+      else if (k == 1) { yf = y + 1 == g.L ? 0 : y + 1; yb = y == 0 ? g.L - 1 : y - 1; }
+      else { zf = z + 1 == g.L ? 0 : z + 1; zb = z == 0 ? g.L - 1 : z - 1; }
+      const int mf = xf + g.L * (yf + g.L * zf), mb = xb + g.L * (yb + g.L * zb);
+      Cx<R> uf[3][3], ub[3][3], vf[3], vb[3];
+      load_link3(U, k, s, (size_t)g.V, uf);
+      load_link3(U, k, (size_t)(t0 + tl) * g.Vs + mb, (size_t)g.V, ub);
 #pragma unroll
-      for (int b = 0; b < 3; b++) {
-        double2 uf = __ldg(U3 + ((size_t)k * 9 + a * 3 + b) * g.V + s);
-        double2 ub = __ldg(U3 + ((size_t)k * 9 + b * 3 + a) * g.V + sb);
-        fma_acc(h, cx<double>(uf.x, uf.y), vf[b]);
-        fma_conj_acc(h, cx<double>(ub.x, ub.y), vb[b]);
+      for (int a = 0; a < 3; a++) {
+        vf[a] = in[((rowbase + mf) * 3 + a) * m + j];
+        vb[a] = in[((rowbase + mb) * 3 + a) * m + j];
       }
-      acc[a] = acc[a] - h;
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        Cx<R> h = cx<R>(0, 0);
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+          fma_acc(h, uf[a][b], vf[b]);
+          fma_conj_acc(h, ub[b][a], vb[b]);
+        }
+        acc[a] = acc[a] - h;
+      }
     }
+#pragma unroll
+    for (int a = 0; a < 3; a++) res[a] = alpha * acc[a] + beta * own[a];
   }
-  double2* o = out + col;
-  const double2* pv = prev ? prev + col : nullptr;
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    Cx<double> r = alpha * acc[a] + beta * own[a];
-    if (pv) {
-      double2 e = pv[(size_t)m * 3 + a];
-      r = r + gamma * cx<double>(e.x, e.y);
+    const size_t idx = ((rowbase + ms) * 3 + a) * m + j;
+    if (prev) res[a] = res[a] + gamma * prev[idx];
+    if (rin) {
+      const R f = alpha * (R)scol[(size_t)tl * m + j];
+      const Cx<float> r = rin[idx];
+      res[a] = res[a] + f * cx<R>((R)r.re, (R)r.im);
     }
-    o[(size_t)m * 3 + a] = make_double2(r.re, r.im);
+    out[idx] = res[a];
   }
 }
 
-// --------------------------------------------------------------------------
 // Gram partials: part[t][split][i][j] = sum_{k in chunk} conj(X_t[k][i]) Y_t[k][j]
 constexpr int GT = 32, GKS = 32;
-__global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ X, const double2* __restrict__ Y, int n,
-                                              int Tn, int m1, int m2, int nsplit, double2* part) {
-  __shared__ double2 xs[GKS][GT + 1];
-  __shared__ double2 ys[GKS][GT + 1];
-  const int tiles_j = (m2 + GT - 1) / GT;
+template <class R>
+__global__ void __launch_bounds__(256) k_gram(const Cx<R>* __restrict__ X, const Cx<R>* __restrict__ Y, int n, int m,
+                                              int nsplit, double2* part) {
+  __shared__ Cx<R> xs[GKS][GT + 1];
+  __shared__ Cx<R> ys[GKS][GT + 1];
+  const int tiles_j = (m + GT - 1) / GT;
   const int i0 = (blockIdx.x / tiles_j) * GT, j0 = (blockIdx.x % tiles_j) * GT;
   const int split = blockIdx.y, t = blockIdx.z;
   const int chunk = (n + nsplit - 1) / nsplit;
   const int k0 = split * chunk, k1 = min(n, k0 + chunk);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4, tid = threadIdx.x;
-  Cx<double> acc[2][2];
+  const Cx<R>* Xt = X + (size_t)t * n * m;
+  const Cx<R>* Yt = Y + (size_t)t * n * m;
+  Cx<R> acc[2][2];
 #pragma unroll
   for (int a = 0; a < 2; a++)
 #pragma unroll
-    for (int b = 0; b < 2; b++) acc[a][b] = cx<double>(0, 0);
+    for (int b = 0; b < 2; b++) acc[a][b] = cx<R>(0, 0);
   for (int kb = k0; kb < k1; kb += GKS) {
 #pragma unroll
     for (int q = 0; q < (GKS * GT) / 256; q++) {
-      int e = tid + 256 * q;
-      int c = e / GKS, r = e % GKS;
-      int k = kb + r;
-      double2 vx = make_double2(0, 0), vy = make_double2(0, 0);
+      const int e = tid + 256 * q;
+      const int r = e / GT, c = e % GT;
+      const int k = kb + r;
+      Cx<R> vx = cx<R>(0, 0), vy = cx<R>(0, 0);
       if (k < k1) {
-        if (i0 + c < m1) vx = X[((size_t)(i0 + c) * Tn + t) * n + k];
-        if (j0 + c < m2) vy = Y[((size_t)(j0 + c) * Tn + t) * n + k];
+        if (i0 + c < m) vx = Xt[(size_t)k * m + i0 + c];
+        if (j0 + c < m) vy = Yt[(size_t)k * m + j0 + c];
       }
       xs[r][c] = vx;
       ys[r][c] = vy;
@@ -120,11 +161,11 @@ __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ X, con
     __syncthreads();
 #pragma unroll 8
     for (int r = 0; r < GKS; r++) {
-      double2 x0 = xs[r][ty], x1 = xs[r][ty + 16], y0 = ys[r][tx], y1 = ys[r][tx + 16];
-      fma_conj_acc(acc[0][0], cx<double>(x0.x, x0.y), cx<double>(y0.x, y0.y));
-      fma_conj_acc(acc[0][1], cx<double>(x0.x, x0.y), cx<double>(y1.x, y1.y));
-      fma_conj_acc(acc[1][0], cx<double>(x1.x, x1.y), cx<double>(y0.x, y0.y));
-      fma_conj_acc(acc[1][1], cx<double>(x1.x, x1.y), cx<double>(y1.x, y1.y));
+      const Cx<R> x0 = xs[r][ty], x1 = xs[r][ty + 16], y0 = ys[r][tx], y1 = ys[r][tx + 16];
+      fma_conj_acc(acc[0][0], x0, y0);
+      fma_conj_acc(acc[0][1], x0, y1);
+      fma_conj_acc(acc[1][0], x1, y0);
+      fma_conj_acc(acc[1][1], x1, y1);
     }
     __syncthreads();
   }
@@ -132,250 +173,123 @@ __global__ void __launch_bounds__(256) k_gram(const double2* __restrict__ X, con
   for (int a = 0; a < 2; a++)
 #pragma unroll
     for (int b = 0; b < 2; b++) {
-      int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
-      if (i < m1 && j < m2) part[(((size_t)t * nsplit + split) * m1 + i) * m2 + j] = make_double2(acc[a][b].re, acc[a][b].im);
+      const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+      if (i < m && j < m)
+        part[(((size_t)t * nsplit + split) * m + i) * m + j] = make_double2((double)acc[a][b].re, (double)acc[a][b].im);
     }
 }
 
-__global__ void k_gram_reduce(const double2* part, int nsplit, int m1, int m2, int Tn, double2* G) {
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t per = (size_t)m1 * m2;
+__global__ void k_gram_reduce(const double2* part, int nsplit, int m, int Tn, double2* G) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t per = (size_t)m * m;
   if (e >= per * Tn) return;
-  size_t t = e / per, ij = e % per;
+  const size_t t = e / per, ij = e % per;
   double2 s = make_double2(0, 0);
   for (int q = 0; q < nsplit; q++) {
-    double2 v = part[(t * nsplit + q) * per + ij];
+    const double2 v = part[(t * nsplit + q) * per + ij];
     s.x += v.x;
     s.y += v.y;
   }
   G[e] = s;
 }
 
-// --------------------------------------------------------------------------
-// rotation: Z_t[k][j] = sum_l X_t[k][l] C_t[l][j], C_t [m1][m2] row-major
-constexpr int RJ = 16;
-__global__ void __launch_bounds__(128) k_rotate(const double2* __restrict__ X, const double2* __restrict__ Cm, int n,
-                                                int Tn, int m1, int m2, double2* __restrict__ Z) {
-  extern __shared__ double2 cs[];          // [m1][RJ]
-  const int t = blockIdx.z, j0 = blockIdx.y * RJ;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const double2* C = Cm + (size_t)t * m1 * m2;
-  for (int e = threadIdx.x; e < m1 * RJ; e += blockDim.x) {
-    int l = e / RJ, jj = e % RJ;
-    cs[e] = (j0 + jj < m2) ? C[(size_t)l * m2 + j0 + jj] : make_double2(0, 0);
-  }
-  __syncthreads();
-  if (k >= n) return;
-  Cx<double> acc[RJ];
+// rotation Z_t = X_t C_t (X_t n x m row-major, C_t m x m row-major FP64); 64 x 64 output tiles
+constexpr int RT = 64, RL = 16;
+template <class R>
+__global__ void __launch_bounds__(256) k_rotate(const Cx<R>* __restrict__ X, const double2* __restrict__ Cm, int n,
+                                                int m, Cx<R>* __restrict__ Z) {
+  __shared__ Cx<R> xs[RT][RL + 1];
+  __shared__ Cx<R> cs[RL][RT + 1];
+  const int t = blockIdx.z, k0 = blockIdx.x * RT, j0 = blockIdx.y * RT;
+  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+  const Cx<R>* Xt = X + (size_t)t * n * m;
+  const double2* C = Cm + (size_t)t * m * m;
+  Cx<R> acc[4][4];
 #pragma unroll
-  for (int jj = 0; jj < RJ; jj++) acc[jj] = cx<double>(0, 0);
-  for (int l = 0; l < m1; l++) {
-    double2 xv = __ldg(X + ((size_t)l * Tn + t) * n + k);
-    Cx<double> x = cx<double>(xv.x, xv.y);
+  for (int a = 0; a < 4; a++)
 #pragma unroll
-    for (int jj = 0; jj < RJ; jj++) {
-      double2 c = cs[l * RJ + jj];
-      fma_acc(acc[jj], x, cx<double>(c.x, c.y));
+    for (int b = 0; b < 4; b++) acc[a][b] = cx<R>(0, 0);
+  for (int l0 = 0; l0 < m; l0 += RL) {
+#pragma unroll
+    for (int q = 0; q < (RT * RL) / 256; q++) {
+      const int e = tid + 256 * q;
+      const int r = e / RL, c = e % RL;
+      const int k = k0 + r, l = l0 + c;
+      xs[r][c] = (k < n && l < m) ? Xt[(size_t)k * m + l] : cx<R>(0, 0);
+      const int r2 = e / RT, c2 = e % RT;
+      const int l2 = l0 + r2, j2 = j0 + c2;
+      double2 cv = (l2 < m && j2 < m) ? C[(size_t)l2 * m + j2] : make_double2(0, 0);
+      cs[r2][c2] = cx<R>((R)cv.x, (R)cv.y);
     }
-  }
-#pragma unroll
-  for (int jj = 0; jj < RJ; jj++)
-    if (j0 + jj < m2) Z[((size_t)(j0 + jj) * Tn + t) * n + k] = make_double2(acc[jj].re, acc[jj].im);
-}
-
-// --------------------------------------------------------------------------
-// small dense hermitian eigenproblems (parallel cyclic Jacobi), one CTA per timeslice
-__device__ __forceinline__ int rr_pos(int idx, int r, int m) { return idx == 0 ? 0 : ((idx - 1 + r) % (m - 1)) + 1; }
-
-// Diagonalise the hermitian A [m][m] (row-major, in place) and accumulate the
-// eigenvectors into V (columns); V must hold the initial basis.
-__device__ void jacobi(double2* A, double2* V, int m, double* rc, double* rs, double2* re, double* red) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int np = m / 2;
-  for (int sweep = 0; sweep < 40; sweep++) {
-    // convergence: off-diagonal vs diagonal
-    double off = 0, dia = 0;
-    for (int e = tid; e < m * m; e += nt) {
-      int i = e / m, j = e % m;
-      double2 v = A[e];
-      if (i == j) dia += v.x * v.x;
-      else off += v.x * v.x + v.y * v.y;
-    }
-    red[tid] = off;
-    red[nt + tid] = dia;
     __syncthreads();
-    for (int s = nt / 2; s > 0; s >>= 1) {
-      if (tid < s) { red[tid] += red[tid + s]; red[nt + tid] += red[nt + tid + s]; }
-      __syncthreads();
+#pragma unroll
+    for (int l = 0; l < RL; l++) {
+      Cx<R> xv[4], cv[4];
+#pragma unroll
+      for (int a = 0; a < 4; a++) xv[a] = xs[tr + 16 * a][l];
+#pragma unroll
+      for (int b = 0; b < 4; b++) cv[b] = cs[l][tc + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) fma_acc(acc[a][b], xv[a], cv[b]);
     }
-    bool done = red[0] <= 1e-30 * red[nt] || red[0] == 0.0;
     __syncthreads();
-    if (done) break;
-    for (int r = 0; r < m - 1; r++) {
-      for (int k = tid; k < np; k += nt) {
-        int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
-        double a = A[p * m + p].x, d = A[q * m + q].x;
-        double2 b = A[p * m + q];
-        double ab = sqrt(b.x * b.x + b.y * b.y);
-        if (ab < 1e-300) { rc[k] = 1; rs[k] = 0; re[k] = make_double2(1, 0); continue; }
-        double tau = (d - a) / (2 * ab);
-        double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1 + tau * tau));
-        double c = 1 / sqrt(1 + tt * tt);
-        rc[k] = c;
-        rs[k] = tt * c;
-        re[k] = make_double2(b.x / ab, -b.y / ab);   // e^{-i phi}
-      }
-      __syncthreads();
-      // A <- A J and V <- V J (columns p, q)
-      for (int e = tid; e < np * m; e += nt) {
-        int k = e / m, i = e % m;
-        int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
-        Cx<double> c = cx<double>(rc[k], 0), s = cx<double>(rs[k], 0), ph = cx<double>(re[k].x, re[k].y);
-        Cx<double> ap = cx<double>(A[i * m + p].x, A[i * m + p].y), aq = cx<double>(A[i * m + q].x, A[i * m + q].y);
-        Cx<double> np_ = c * ap - s * (ph * aq), nq = s * ap + c * (ph * aq);
-        A[i * m + p] = make_double2(np_.re, np_.im);
-        A[i * m + q] = make_double2(nq.re, nq.im);
-        Cx<double> vp = cx<double>(V[i * m + p].x, V[i * m + p].y), vq = cx<double>(V[i * m + q].x, V[i * m + q].y);
-        np_ = c * vp - s * (ph * vq);
-        nq = s * vp + c * (ph * vq);
-        V[i * m + p] = make_double2(np_.re, np_.im);
-        V[i * m + q] = make_double2(nq.re, nq.im);
-      }
-      __syncthreads();
-      // A <- J^dag A (rows p, q)
-      for (int e = tid; e < np * m; e += nt) {
-        int k = e / m, j = e % m;
-        int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
-        Cx<double> c = cx<double>(rc[k], 0), s = cx<double>(rs[k], 0), ph = conj(cx<double>(re[k].x, re[k].y));
-        Cx<double> ap = cx<double>(A[p * m + j].x, A[p * m + j].y), aq = cx<double>(A[q * m + j].x, A[q * m + j].y);
-        Cx<double> np_ = c * ap - s * (ph * aq), nq = s * ap + c * (ph * aq);
-        A[p * m + j] = make_double2(np_.re, np_.im);
-        A[q * m + j] = make_double2(nq.re, nq.im);
-      }
-      __syncthreads();
-    }
   }
+  Cx<R>* Zt = Z + (size_t)t * n * m;
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const int k = k0 + tr + 16 * a, j = j0 + tc + 16 * b;
+      if (k < n && j < m) Zt[(size_t)k * m + j] = acc[a][b];
+    }
 }
 
-// Rayleigh-Ritz on one timeslice: from G = Y^dag Y and H = Y^dag A Y produce C
-// (Y C orthonormal Ritz vectors, ascending Ritz values theta).  Work: 3 m x m buffers.
-__global__ void __launch_bounds__(256) k_small_rr(const double2* Gall, const double2* Hall, int m, double2* Call,
-                                                  double* theta_all, double2* gwork, int use_smem, int* dropped) {
-  extern __shared__ double2 sm[];
-  const int t = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const size_t mm = (size_t)m * m;
-  double2 *S, *A, *Z;
-  if (use_smem) { S = sm; A = sm + mm; Z = sm + 2 * mm; }
-  else { S = gwork + 3 * mm * t; A = S + mm; Z = A + mm; }
-  __shared__ double rc[128], rs[128], red[512], lam[256];
-  __shared__ double2 re[128];
-  __shared__ int order[256];
-  const double2* G = Gall + mm * t;
-  const double2* H = Hall + mm * t;
-  // 1) eigen-decomposition of the Gram matrix
-  for (size_t e = tid; e < mm; e += nt) {
-    A[e] = G[e];
-    S[e] = make_double2((e / m) == (e % m) ? 1.0 : 0.0, 0.0);
-  }
-  __syncthreads();
-  jacobi(A, S, m, rc, rs, re, red);
-  // 2) S <- Q diag(g)^-1/2, dropping directions with g <= 1e-24 gmax (round-off level)
-  if (tid == 0) {
-    double gmax = 0;
-    for (int i = 0; i < m; i++) gmax = fmax(gmax, A[i * m + i].x);
-    red[0] = gmax;
-  }
-  __syncthreads();
-  const double gmax = red[0];
-  __syncthreads();
-  for (int i = tid; i < m; i += nt) {
-    double gi = A[i * m + i].x;
-    lam[i] = gi > 1e-24 * gmax ? 1.0 / sqrt(gi) : 0.0;
-  }
-  __syncthreads();
-  for (size_t e = tid; e < mm; e += nt) {
-    int j = e % m;
-    S[e] = make_double2(S[e].x * lam[j], S[e].y * lam[j]);
-  }
-  __syncthreads();
-  // 3) Z <- H S ; A <- S^dag Z  (= S^dag H S)
-  for (size_t e = tid; e < mm; e += nt) {
-    int i = e / m, j = e % m;
-    Cx<double> s = cx<double>(0, 0);
-    for (int l = 0; l < m; l++) fma_acc(s, cx<double>(H[i * m + l].x, H[i * m + l].y), cx<double>(S[l * m + j].x, S[l * m + j].y));
-    Z[e] = make_double2(s.re, s.im);
-  }
-  __syncthreads();
-  for (size_t e = tid; e < mm; e += nt) {
-    int i = e / m, j = e % m;
-    Cx<double> s = cx<double>(0, 0);
-    for (int l = 0; l < m; l++) fma_conj_acc(s, cx<double>(S[l * m + i].x, S[l * m + i].y), cx<double>(Z[l * m + j].x, Z[l * m + j].y));
-    A[e] = make_double2(s.re, s.im);
-  }
-  __syncthreads();
-  // symmetrise (round-off) and reset Z to the identity
-  for (size_t e = tid; e < mm; e += nt) {
-    int i = e / m, j = e % m;
-    if (i < j) {
-      double2 a = A[i * m + j], b = A[j * m + i];
-      double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
-      A[i * m + j] = h;
-      A[j * m + i] = make_double2(h.x, -h.y);
-    } else if (i == j) {
-      A[e].y = 0;
-    }
-  }
-  for (size_t e = tid; e < mm; e += nt) Z[e] = make_double2((e / m) == (e % m) ? 1.0 : 0.0, 0.0);
-  __syncthreads();
-  jacobi(A, Z, m, rc, rs, re, red);
-  // 4) sort ascending; dropped directions (zero S column) sort last
-  for (int i = tid; i < m; i += nt) lam[i] = lam[i] > 0 ? A[i * m + i].x : 1e300;
-  __syncthreads();
-  // (a dropped direction i has an exactly zero row and column in S^dag H S, so
-  //  Jacobi never rotates it and it keeps diagonal position i: sorted last above)
-  for (int i = tid; i < m; i += nt) {
-    int rank = 0;
-    for (int l = 0; l < m; l++) rank += (lam[l] < lam[i]) || (lam[l] == lam[i] && l < i);
-    order[rank] = i;
-  }
-  __syncthreads();
-  // 5) C = S Z[:, order]
-  double2* Cout = Call + mm * t;
-  for (size_t e = tid; e < mm; e += nt) {
-    int i = e / m, j = e % m;
-    int zj = order[j];
-    Cx<double> s = cx<double>(0, 0);
-    for (int l = 0; l < m; l++) fma_acc(s, cx<double>(S[i * m + l].x, S[i * m + l].y), cx<double>(Z[l * m + zj].x, Z[l * m + zj].y));
-    Cout[e] = make_double2(s.re, s.im);
-  }
-  for (int j = tid; j < m; j += nt) {
-    double v = lam[order[j]];
-    theta_all[(size_t)t * m + j] = v;
-    if (v > 1e299) atomicAdd(dropped, 1);
-  }
-}
-
-// residual norms res[t][j] = ||W_j - theta_j X_j|| for the batch
-__global__ void k_resid(const double2* __restrict__ X, const double2* __restrict__ W, const double* theta, int n,
-                        int Tn, int m, double* res) {
-  const int j = blockIdx.x, t = blockIdx.y;
-  const double th = theta[(size_t)t * m + j];
-  const double2* x = X + ((size_t)j * Tn + t) * n;
-  const double2* w = W + ((size_t)j * Tn + t) * n;
+// residual norms res[t][j] = ||W_j - theta_j X_j||; optionally R = W - X Theta stored in FP32
+template <class R>
+__global__ void __launch_bounds__(256) k_resid(const Cx<R>* __restrict__ X, const Cx<R>* __restrict__ W,
+                                               const double* __restrict__ theta, int n, int m, double* res,
+                                               Cx<float>* Rout) {
+  const int t = blockIdx.y;
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31), lane = threadIdx.x >> 5;
   double s = 0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    double2 a = w[k], b = x[k];
-    double dx = a.x - th * b.x, dy = a.y - th * b.y;
-    s += dx * dx + dy * dy;
+  if (j < m) {
+    const double th = theta[(size_t)t * m + j];
+    const size_t base = (size_t)t * n * m;
+    for (int k = lane; k < n; k += 8) {
+      const size_t idx = base + (size_t)k * m + j;
+      const Cx<R> w = W[idx], x = X[idx];
+      const double dx = (double)w.re - th * (double)x.re, dy = (double)w.im - th * (double)x.im;
+      s += dx * dx + dy * dy;
+      if (Rout) Rout[idx] = cx<float>((float)dx, (float)dy);
+    }
   }
-  __shared__ double red[256];
-  red[threadIdx.x] = s;
+  __shared__ double red[8][33];
+  red[lane][threadIdx.x & 31] = s;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if (lane == 0 && j < m) {
+    double tot = 0;
+    for (int q = 0; q < 8; q++) tot += red[q][threadIdx.x];
+    res[(size_t)t * m + j] = sqrt(tot);
   }
-  if (threadIdx.x == 0) res[(size_t)t * m + j] = sqrt(red[0]);
+}
+
+// Y64 = X64 s[t][j] + E32  (phase B filter output)
+__global__ void k_combine(const Cx<double>* __restrict__ X, const Cx<float>* __restrict__ E,
+                          const double* __restrict__ scol, size_t nm, int m, size_t total, Cx<double>* Y) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int j = e % m;
+  const size_t t = e / nm;
+  const double s = scol[t * m + j];
+  const Cx<float> ev = E[e];
+  Y[e] = s * X[e] + cx<double>((double)ev.re, (double)ev.im);
+}
+
+template <class A, class B> __global__ void k_convert_block(const Cx<A>* in, Cx<B>* out, size_t total) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < total) out[e] = cx<B>((B)in[e].re, (B)in[e].im);
 }
 
 // counter-based start vectors: splitmix64 of (seed, index) -> two uniforms in (-1, 1)
@@ -385,204 +299,405 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
   return z ^ (z >> 31);
 }
-__global__ void k_random(double2* X, size_t count, uint64_t seed) {
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_random(Cx<float>* X, size_t count, uint64_t seed) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= count) return;
-  uint64_t h = splitmix64(seed ^ splitmix64(e));
-  double a = (double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
-  uint64_t h2 = splitmix64(h);
-  double b = (double)(h2 >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
-  X[e] = make_double2(a, b);
+  const uint64_t h = splitmix64(seed ^ splitmix64(e));
+  const double a = (double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  const uint64_t h2 = splitmix64(h);
+  const double b = (double)(h2 >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  X[e] = cx<float>((float)a, (float)b);
 }
 
-// copy the first N columns of the block into evecs [Tn][N][Vs][3] (or the cache layout [N][T][Vs][3])
-__global__ void k_extract(const double2* X, int n, int Tn, int N, double2* out, int cache_layout, int T, int t0) {
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t total = (size_t)N * Tn * n;
+// columns whose Ritz value is marked dropped (>= 1e299) get fresh random entries
+template <class R>
+__global__ void k_refill(Cx<R>* X, const double* theta, int n, int m, size_t total, uint64_t seed) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= total) return;
-  size_t k = e % n;
-  size_t rest = e / n;
-  int t = rest % Tn;
-  int j = rest / Tn;
-  double2 v = X[((size_t)j * Tn + t) * n + k];
-  if (cache_layout) out[((size_t)j * T + t0 + t) * n + k] = v;
-  else out[((size_t)t * N + j) * n + k] = v;
+  const int j = e % m;
+  const size_t t = e / ((size_t)n * m);
+  if (theta[t * m + j] < 1e299) return;
+  const uint64_t h = splitmix64(seed ^ splitmix64(e));
+  const uint64_t h2 = splitmix64(h);
+  X[e] = cx<R>((R)((double)(h >> 11) * (2.0 / 9007199254740992.0) - 1.0),
+               (R)((double)(h2 >> 11) * (2.0 / 9007199254740992.0) - 1.0));
+}
+
+// first N columns of the block -> out [Tn][N][Vs][3] (cache_layout: [N][T][Vs][3] at timeslice t0 + t)
+__global__ void k_extract(const Cx<double>* X, int n, int Tn, int m, int N, double2* out, int cache_layout, int T,
+                          int t0) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t total = (size_t)N * Tn * n;
+  if (e >= total) return;
+  const size_t r = e % n;
+  const size_t rest = e / n;
+  const int k = rest % N;
+  const int t = rest / N;
+  const Cx<double> v = X[((size_t)t * n + r) * m + k];
+  const size_t o = cache_layout ? ((size_t)k * T + t0 + t) * n + r : ((size_t)t * N + k) * n + r;
+  out[o] = make_double2(v.re, v.im);
+}
+
+// the original per-vector layout ([nvec][V][3]) for dlma_apply_laplacian
+__global__ void k_lap_canonical(Geom g, const double2* __restrict__ U3, const double2* __restrict__ in, double2* out,
+                                int nvec) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (s >= g.V || j >= nvec) return;
+  const int x = s % g.L, y = (s / g.L) % g.L, z = (s / (g.L * g.L)) % g.L, t = s / g.Vs;
+  const Coord c{x, y, z, t};
+  const double2* v = in + (size_t)j * g.V * 3;
+  Cx<double> acc[3];
+  for (int a = 0; a < 3; a++) {
+    const double2 e = v[(size_t)s * 3 + a];
+    acc[a] = cx<double>(-6.0 * e.x, -6.0 * e.y);
+  }
+  for (int k = 0; k < 3; k++) {
+    const int nf = nbr_lex(g, c, k + 1, +1), nb = nbr_lex(g, c, k + 1, -1);
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) {
+        const double2 uf = U3[((size_t)k * 9 + a * 3 + b) * g.V + s];
+        const double2 ub = U3[((size_t)k * 9 + b * 3 + a) * g.V + nb];
+        const double2 vf = v[(size_t)nf * 3 + b], vb = v[(size_t)nb * 3 + b];
+        fma_acc(acc[a], cx<double>(uf.x, uf.y), cx<double>(vf.x, vf.y));
+        fma_conj_acc(acc[a], cx<double>(ub.x, ub.y), cx<double>(vb.x, vb.y));
+      }
+  }
+  double2* o = out + (size_t)j * g.V * 3;
+  for (int a = 0; a < 3; a++) o[(size_t)s * 3 + a] = make_double2(acc[a].re, acc[a].im);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-struct EigBufs {
-  double2 *X, *Y, *Yn, *W, *G, *H, *part, *C, *gwork;
-  double *theta, *res, *coef;
+struct Eig {
+  dlma_ctx* ctx;
+  int t0, Tn, N, m, n, nsplit, degree;
+  size_t blk;                    // m * Tn * n complex entries per block
+  Cx<float> *F0, *F1, *F2, *F3;  // FP32 blocks
+  Cx<double> *D0, *D1, *D2;      // FP64 blocks
+  double2 *G, *H, *C, *part, *gwork;
+  double *theta, *res, *coef, *scol;
   int* dropped;
+  double drop_rel;
+  uint64_t refill_seed;
+  std::vector<double> th, rs;
 };
 
-static dlma_status lap_apply_batch(dlma_ctx* ctx, int t0, int Tn, int m, const double2* in, const double2* prev,
-                                   double2* out, const double* coef) {
-  dim3 grid((Tn * ctx->g.Vs + 127) / 128, m);
-  k_lap_fused<<<grid, 128, 0, ctx->stream>>>(ctx->g, t0, Tn, ctx->U3, in, prev, out, m, coef);
+template <class R> static const typename LinkT<R>::T* links(dlma_ctx* ctx);
+template <> const double2* links<double>(dlma_ctx* ctx) { return ctx->U3; }
+template <> const float4* links<float>(dlma_ctx* ctx) { return ctx->U3f; }
+
+template <class R>
+static dlma_status lap(Eig& E, const Cx<R>* in, const Cx<R>* prev, const Cx<float>* rin, const double* scol,
+                       Cx<R>* out, const double* coef) {
+  dlma_ctx* ctx = E.ctx;
+  const size_t total = (size_t)E.Tn * ctx->g.Vs * E.m;
+  k_lap<R><<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(ctx->g, E.t0, E.Tn, E.m, links<R>(ctx), in, prev,
+                                                                     rin, scol, out, coef);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
 
-static dlma_status gram(dlma_ctx* ctx, const double2* X, const double2* Y, int n, int Tn, int m, EigBufs& B,
-                        double2* out, int nsplit) {
-  int tiles = ((m + GT - 1) / GT) * ((m + GT - 1) / GT);
-  dim3 grid(tiles, nsplit, Tn);
-  k_gram<<<grid, 256, 0, ctx->stream>>>(X, Y, n, Tn, m, m, nsplit, B.part);
+template <class R> static dlma_status gram(Eig& E, const Cx<R>* X, const Cx<R>* Y, double2* out) {
+  dlma_ctx* ctx = E.ctx;
+  const int tiles = ((E.m + GT - 1) / GT) * ((E.m + GT - 1) / GT);
+  k_gram<R><<<dim3(tiles, E.nsplit, E.Tn), 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, E.part);
   CHECK_LAUNCH();
-  size_t tot = (size_t)m * m * Tn;
-  k_gram_reduce<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(B.part, nsplit, m, m, Tn, out);
-  CHECK_LAUNCH();
-  return DLMA_OK;
-}
-
-static dlma_status rotate(dlma_ctx* ctx, const double2* X, const double2* C, int n, int Tn, int m, double2* Z) {
-  dim3 grid((n + 127) / 128, (m + RJ - 1) / RJ, Tn);
-  size_t sm = (size_t)m * RJ * sizeof(double2);
-  if (sm > 48 * 1024) CU(cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_rotate<<<grid, 128, sm, ctx->stream>>>(X, C, n, Tn, m, m, Z);
+  const size_t tot = (size_t)E.m * E.m * E.Tn;
+  k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(E.part, E.nsplit, E.m, E.Tn, out);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
 
-static dlma_status small_rr(dlma_ctx* ctx, EigBufs& B, int Tn, int m) {
-  size_t sm = (size_t)3 * m * m * sizeof(double2);
+template <class R> static dlma_status rotate(Eig& E, const Cx<R>* X, Cx<R>* Z) {
+  dlma_ctx* ctx = E.ctx;
+  k_rotate<R><<<dim3((E.n + RT - 1) / RT, (E.m + RT - 1) / RT, E.Tn), 256, 0, ctx->stream>>>(X, E.C, E.n, E.m, Z);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+// small Rayleigh-Ritz problems in precision T (float in phase A, double in phase B)
+template <class T> static dlma_status small_rr(Eig& E) {
+  dlma_ctx* ctx = E.ctx;
+  const size_t sm = (size_t)3 * E.m * E.m * sizeof(Cx<T>);
   // the kernel also holds ~11 KB of static shared memory: always raise the dynamic limit
-  int use_smem = sm <= 200 * 1024;
-  if (use_smem) CU(cudaFuncSetAttribute(k_small_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_small_rr<<<Tn, 256, use_smem ? sm : 0, ctx->stream>>>(B.G, B.H, m, B.C, B.theta, B.gwork, use_smem, B.dropped);
+  const int use_smem = sm <= 200 * 1024;
+  if (use_smem) CU(cudaFuncSetAttribute(k_small_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  CU(cudaMemsetAsync(E.dropped, 0, sizeof(int), ctx->stream));
+  k_small_rr<T><<<E.Tn, 256, use_smem ? sm : 0, ctx->stream>>>(E.G, E.H, E.m, E.C, E.theta, (Cx<T>*)E.gwork,
+                                                               use_smem, E.dropped, E.drop_rel);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
 
-// One Rayleigh-Ritz step on the block Y (with W = A Y computed here):
-// X <- Y C, Wx <- W C, theta, residual norms.  Y, W are clobbered only via outputs.
-static dlma_status rayleigh_ritz(dlma_ctx* ctx, EigBufs& B, int t0, int Tn, int m, int n, double2* Yblk,
-                                 double2* Wblk, double2* Xout, double2* Wout, int nsplit) {
-  // W = A Y (alpha 1, beta 0)
-  TRY(lap_apply_batch(ctx, t0, Tn, m, Yblk, nullptr, Wblk, B.coef));
-  TRY(gram(ctx, Yblk, Yblk, n, Tn, m, B, B.G, nsplit));
-  TRY(gram(ctx, Yblk, Wblk, n, Tn, m, B, B.H, nsplit));
-  CU(cudaMemsetAsync(B.dropped, 0, sizeof(int), ctx->stream));
-  TRY(small_rr(ctx, B, Tn, m));
-  TRY(rotate(ctx, Yblk, B.C, n, Tn, m, Xout));
-  TRY(rotate(ctx, Wblk, B.C, n, Tn, m, Wout));
-  k_resid<<<dim3(m, Tn), 256, 0, ctx->stream>>>(Xout, Wout, B.theta, n, Tn, m, B.res);
+// Rayleigh-Ritz of the block Y: W = A Y, then X <- Y C, AX <- W C, residuals (and R = AX - X Theta in FP32)
+template <class R>
+static dlma_status rayleigh_ritz(Eig& E, Cx<R>* Y, Cx<R>* W, Cx<R>* Xout, Cx<R>* AXout, Cx<float>* Rout,
+                                 const double* coef_plain) {
+  TRY(lap<R>(E, Y, nullptr, nullptr, nullptr, W, coef_plain));
+  TRY(gram<R>(E, Y, Y, E.G));
+  TRY(gram<R>(E, Y, W, E.H));
+  TRY(small_rr<R>(E));
+  TRY(rotate<R>(E, Y, Xout));
+  TRY(rotate<R>(E, W, AXout));
+  dlma_ctx* ctx = E.ctx;
+  k_resid<R><<<dim3((E.m + 31) / 32, E.Tn), 256, 0, ctx->stream>>>(Xout, AXout, E.theta, E.n, E.m, E.res, Rout);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
 
-// Modes of timeslices [t0, t0 + Tn): eigenvalues into lam_out [Tn][N] (host), vectors into the block X
-static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, double* lam_out, double2** Xres,
-                             int* m_out) {
-  const int n = 3 * ctx->g.Vs;
-  int buf = std::max(8, (N + 3) / 4);
+// fetch theta / residuals; returns the worst relative residual over the wanted pairs.
+// Dropped directions (buffer columns that fell below the block's rounding level)
+// are refilled with random entries in X and get the largest finite Ritz value of
+// their timeslice on the host, so the filter's cut stays finite.
+template <class R> static dlma_status fetch(Eig& E, double* worst, Cx<R>* X) {
+  dlma_ctx* ctx = E.ctx;
+  const size_t cnt = (size_t)E.m * E.Tn;
+  CU(cudaMemcpyAsync(E.th.data(), E.theta, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(E.rs.data(), E.res, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+  int hdrop = 0;
+  CU(cudaMemcpyAsync(&hdrop, E.dropped, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (hdrop) {
+    k_refill<R><<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X, E.theta, E.n, E.m, E.blk,
+                                                                         E.refill_seed++);
+    CHECK_LAUNCH();
+    for (int t = 0; t < E.Tn; t++) {
+      double mx = 0;
+      for (int j = 0; j < E.m; j++) {
+        const double v = E.th[(size_t)t * E.m + j];
+        if (v < 1e299) mx = std::max(mx, v);
+      }
+      for (int j = 0; j < E.m; j++) {
+        double& v = E.th[(size_t)t * E.m + j];
+        if (v >= 1e299) { v = mx; E.rs[(size_t)t * E.m + j] = 1.0; }
+      }
+    }
+  }
+  double w = 0;
+  for (int t = 0; t < E.Tn; t++)
+    for (int k = 0; k < E.N; k++) {
+      const double r = E.rs[(size_t)t * E.m + k] / std::max(1.0, fabs(E.th[(size_t)t * E.m + k]));
+      if (!(r == r)) return set_err(ctx, DLMA_ERR_NONFINITE, "NaN in the eigensolver");
+      w = std::max(w, r);
+    }
+  *worst = w;
+  return DLMA_OK;
+}
+
+// largest degree (<= dmax) whose amplification across [theta_0, cut] stays below rho on every timeslice
+static int safe_degree(const Eig& E, double rho, int dmax) {
+  int d = dmax;
+  for (int t = 0; t < E.Tn; t++) {
+    double a = E.th[(size_t)t * E.m + E.m - 1], a0 = E.th[(size_t)t * E.m];
+    const double b = 12.0;
+    if (a >= b) a = 0.5 * (a0 + b);
+    const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    const double x0 = (c - a0) / e;
+    if (x0 > 1.0) d = std::min(d, (int)(acosh(rho) / acosh(x0)));
+  }
+  return std::max(d, 2);
+}
+
+// Chebyshev coefficients of every step (scaled three-term recurrence damping [cut_t, 12],
+// normalised at lam0_t): slot 0 = first step, slot k-1 = step k; slot `degree` = plain A.
+// With s_k(theta) (the scalar recurrence at each Ritz value) when scol != nullptr.
+static void cheb_coefficients(Eig& E, int d, std::vector<double>& hc, std::vector<double>* hs) {
+  const int Tn = E.Tn, m = E.m;
+  hc.assign((size_t)(E.degree + 1) * 3 * Tn, 0.0);
+  if (hs) hs->assign((size_t)(E.degree + 1) * Tn * m, 0.0);
+  for (int t = 0; t < Tn; t++) {
+    double a = E.th[(size_t)t * m + m - 1], a0 = E.th[(size_t)t * m];
+    const double b = 12.0;
+    if (a >= b) a = 0.5 * (a0 + b);
+    const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    double sigma = e / (a0 - c);
+    const double tau = 2.0 / sigma;
+    double* c0 = &hc[3 * t];
+    c0[0] = sigma / e;
+    c0[1] = -c * sigma / e;
+    c0[2] = 0.0;
+    std::vector<double> sp(m, 1.0), sc(m);
+    for (int j = 0; j < m; j++) sc[j] = c0[0] * E.th[(size_t)t * m + j] + c0[1];
+    if (hs) {
+      for (int j = 0; j < m; j++) (*hs)[(size_t)t * m + j] = 1.0;                    // s_0
+      for (int j = 0; j < m; j++) (*hs)[(size_t)Tn * m + (size_t)t * m + j] = sc[j];  // s_1
+    }
+    for (int k = 2; k <= d; k++) {
+      const double sn = 1.0 / (tau - sigma);
+      double* ck = &hc[(size_t)(k - 1) * 3 * Tn + 3 * t];
+      ck[0] = 2.0 * sn / e;
+      ck[1] = -2.0 * c * sn / e;
+      ck[2] = -sigma * sn;
+      sigma = sn;
+      for (int j = 0; j < m; j++) {
+        const double th = E.th[(size_t)t * m + j];
+        const double nv = ck[0] * th * sc[j] + ck[1] * sc[j] + ck[2] * sp[j];
+        sp[j] = sc[j];
+        sc[j] = nv;
+        if (hs) (*hs)[(size_t)k * Tn * m + (size_t)t * m + j] = nv;
+      }
+    }
+    double* cd = &hc[(size_t)E.degree * 3 * Tn + 3 * t];   // slot of the plain A application
+    cd[0] = 1;
+    cd[1] = 0;
+    cd[2] = 0;
+  }
+}
+
+static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, double* lam_out,
+                             Cx<double>** Xres, int* m_out, int* iters_out) {
+  Eig E;
+  E.ctx = ctx;
+  E.t0 = t0;
+  E.Tn = Tn;
+  E.N = N;
+  E.n = 3 * ctx->g.Vs;
+  int buf = std::max(16, std::min(N, 64));
   int m = N + buf;
   m += m & 1;
-  if (m > n) m = n - (n & 1);
+  if (m > E.n) m = E.n - (E.n & 1);
   if (m < N) return set_err(ctx, DLMA_ERR_INVALID_ARG, "N too large for the timeslice");
-  if (m > 254) return set_err(ctx, DLMA_ERR_INVALID_ARG, "N above the eigensolver's limit of 240");
-  const size_t blk = (size_t)m * Tn * n;
-  EigBufs B;
-  TRY(workT(ctx, WS_EIG_X, blk, &B.X));
-  TRY(workT(ctx, WS_EIG_Y, blk, &B.Y));
-  TRY(workT(ctx, WS_EIG_Y2, blk, &B.Yn));
-  TRY(workT(ctx, WS_EIG_W, blk, &B.W));
-  int nsplit = std::max(1, std::min(64, (4 * 152) / std::max(1, Tn * ((m + GT - 1) / GT) * ((m + GT - 1) / GT))));
-  nsplit = std::min(nsplit, std::max(1, n / 256));
+  if (m > 254) return set_err(ctx, DLMA_ERR_INVALID_ARG, "N + buffer above the eigensolver's limit of 254");
+  E.m = m;
+  E.degree = 40;            // largest filter degree (phase B); phase A stays below 20
+  E.blk = (size_t)m * Tn * E.n;
+  E.nsplit = std::max(1, std::min(64, (4 * 152) / std::max(1, Tn * ((m + GT - 1) / GT) * ((m + GT - 1) / GT))));
+  E.nsplit = std::min(E.nsplit, std::max(1, E.n / 256));
+  TRY(workT(ctx, WS_EIG_X, E.blk * 2, &E.F0));
+  E.F1 = E.F0 + E.blk;
+  TRY(workT(ctx, WS_EIG_Y, E.blk * 2, &E.F2));
+  E.F3 = E.F2 + E.blk;
+  TRY(workT(ctx, WS_EIG_Y2, E.blk, &E.D0));
+  TRY(workT(ctx, WS_EIG_W, E.blk * 2, &E.D1));
+  E.D2 = E.D1 + E.blk;
   const size_t mm = (size_t)m * m;
-  TRY(workT(ctx, WS_EIG_G, 3 * mm * Tn, &B.G));
-  B.H = B.G + mm * Tn;
-  B.C = B.H + mm * Tn;
-  TRY(workT(ctx, WS_EIG_PART, (size_t)nsplit * mm * Tn, &B.part));
-  TRY(workT(ctx, WS_EIG_S, 3 * mm * Tn, &B.gwork));
+  TRY(workT(ctx, WS_EIG_G, 3 * mm * Tn, &E.G));
+  E.H = E.G + mm * Tn;
+  E.C = E.H + mm * Tn;
+  TRY(workT(ctx, WS_EIG_PART, (size_t)E.nsplit * mm * Tn, &E.part));
+  TRY(workT(ctx, WS_EIG_S, 3 * mm * Tn, &E.gwork));
+  const int d = E.degree;
   double* aux;
-  TRY(workT(ctx, WS_EIG_AUX, (size_t)2 * m * Tn + 64 * (size_t)Tn * 3 + 16, &aux));
-  B.theta = aux;
-  B.res = aux + (size_t)m * Tn;
-  B.coef = aux + (size_t)2 * m * Tn;
-  B.dropped = (int*)(B.coef + 64 * (size_t)Tn * 3);
+  const size_t ncoef = (size_t)(d + 1) * 3 * Tn, nscol = (size_t)(d + 1) * Tn * m;
+  TRY(workT(ctx, WS_EIG_AUX, 2 * (size_t)m * Tn + ncoef + nscol + 16, &aux));
+  E.theta = aux;
+  E.res = aux + (size_t)m * Tn;
+  E.coef = E.res + (size_t)m * Tn;
+  E.scol = E.coef + ncoef;
+  E.dropped = (int*)(E.scol + nscol);
+  E.th.resize((size_t)m * Tn);
+  E.rs.resize((size_t)m * Tn);
+  E.drop_rel = 1e-10;
+  E.refill_seed = 0x7e11ULL + (uint64_t)t0;
+  std::vector<double> hc, hs;
+  // plain A for the Rayleigh-Ritz W = A Y: coefficient slot d
+  hc.assign(ncoef, 0.0);
+  for (int t = 0; t < Tn; t++) hc[(size_t)d * 3 * Tn + 3 * t] = 1.0;
+  CU(cudaMemcpyAsync(E.coef, hc.data(), sizeof(double) * ncoef, cudaMemcpyHostToDevice, ctx->stream));
+  const double* plain = E.coef + (size_t)d * 3 * Tn;
 
-  std::vector<double> hcoef(64 * 3 * (size_t)Tn);
-  // W = A Y uses alpha 1, beta 0, gamma 0 from the first coefficient slot
-  for (int t = 0; t < Tn; t++) { hcoef[3 * t] = 1; hcoef[3 * t + 1] = 0; hcoef[3 * t + 2] = 0; }
-  CU(cudaMemcpyAsync(B.coef, hcoef.data(), sizeof(double) * 3 * Tn, cudaMemcpyHostToDevice, ctx->stream));
-  k_random<<<(blk + 255) / 256, 256, 0, ctx->stream>>>(B.Y, blk, 0x5eed2022ULL + (uint64_t)t0 * 7919ULL);
+  // ---- phase A: FP32 ----
+  k_random<<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(E.F1, E.blk, 0x5eed2022ULL + (uint64_t)t0 * 7919ULL);
   CHECK_LAUNCH();
-  // initial Rayleigh-Ritz on the random block
-  TRY(rayleigh_ritz(ctx, B, t0, Tn, m, n, B.Y, B.W, B.X, B.Yn, nsplit));
-  std::vector<double> th((size_t)m * Tn), rs((size_t)m * Tn);
-  const int degree = 20;
-  const int max_iter = 400;
+  // three FP32 blocks rotate: p3[0] = Ritz vectors X, p3[1], p3[2] free; F3 holds A X
+  Cx<float>* p3[3] = {E.F0, E.F1, E.F2};
+  TRY(rayleigh_ritz<float>(E, p3[1], p3[2], p3[0], E.F3, nullptr, plain));
+  double worst = 1;
   int it = 0;
-  bool conv = false;
-  for (; it < max_iter; it++) {
-    CU(cudaMemcpyAsync(th.data(), B.theta, sizeof(double) * m * Tn, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(rs.data(), B.res, sizeof(double) * m * Tn, cudaMemcpyDeviceToHost, ctx->stream));
-    int hdrop = 0;
-    CU(cudaMemcpyAsync(&hdrop, B.dropped, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    if (hdrop) return set_err(ctx, DLMA_ERR_NOT_CONVERGED, "eigensolver lost rank (%d directions)", hdrop);
-    double worst = 0;
-    for (int t = 0; t < Tn; t++)
-      for (int k = 0; k < N; k++) {
-        double r = rs[(size_t)t * m + k] / std::max(1.0, fabs(th[(size_t)t * m + k]));
-        if (!(r == r)) return set_err(ctx, DLMA_ERR_NONFINITE, "NaN in the eigensolver");
-        worst = std::max(worst, r);
-      }
-    if (worst <= tol) { conv = true; break; }
-    // Chebyshev filter of degree d damping [cut_t, 12], scaled at lam0_t
-    for (int t = 0; t < Tn; t++) {
-      double a = th[(size_t)t * m + m - 1], a0 = th[(size_t)t * m];
-      double b = 12.0;
-      if (a >= b) a = 0.5 * (a0 + b);
-      double e = 0.5 * (b - a), c = 0.5 * (b + a);
-      double sigma = e / (a0 - c), tau = 2.0 / sigma;
-      hcoef[3 * t + 0] = sigma / e;
-      hcoef[3 * t + 1] = -c * sigma / e;
-      hcoef[3 * t + 2] = 0.0;
-      for (int k = 2; k <= degree; k++) {
-        double sn = 1.0 / (tau - sigma);
-        size_t o = (size_t)(k - 1) * 3 * Tn + 3 * t;
-        hcoef[o + 0] = 2.0 * sn / e;
-        hcoef[o + 1] = -2.0 * c * sn / e;
-        hcoef[o + 2] = -sigma * sn;
-        sigma = sn;
-      }
-      size_t o = (size_t)degree * 3 * Tn + 3 * t;   // slot for the plain A application
-      hcoef[o] = 1; hcoef[o + 1] = 0; hcoef[o + 2] = 0;
-    }
-    CU(cudaMemcpyAsync(B.coef, hcoef.data(), sizeof(double) * 3 * Tn * (degree + 1), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    // three-term recurrence: prev = X, cur = Y
-    double2 *prev = B.X, *cur = B.Y, *nxt = B.Yn;
-    TRY(lap_apply_batch(ctx, t0, Tn, m, prev, nullptr, cur, B.coef));
-    for (int k = 2; k <= degree; k++) {
-      TRY(lap_apply_batch(ctx, t0, Tn, m, cur, prev, nxt, B.coef + (size_t)(k - 1) * 3 * Tn));
-      double2* tmp = prev;
+  const int maxA = 60, maxB = 40;
+  const double switch_tol = std::max(tol, 3e-6);
+  double prev_worst = 1e300;
+  E.drop_rel = 1e-10;       // FP32 block: Gram eigenvalues below ~1e-10 gmax are rounding noise
+  for (; it < maxA; it++) {
+    TRY(fetch<float>(E, &worst, p3[0]));
+    if (worst <= switch_tol) break;
+    // single precision has stopped paying off: hand over to the FP64 phase
+    if (it >= 3 && worst > 0.5 * prev_worst) break;
+    prev_worst = worst;
+    // FP32 filter: keep the amplification across [theta_0, cut] below ~300 so the
+    // filtered block stays resolvable in single precision
+    const int dA = safe_degree(E, 300.0, 20);
+    cheb_coefficients(E, dA, hc, nullptr);
+    CU(cudaMemcpyAsync(E.coef, hc.data(), sizeof(double) * ncoef, cudaMemcpyHostToDevice, ctx->stream));
+    Cx<float>*prev = p3[0], *cur = p3[1], *nxt = p3[2];
+    TRY(lap<float>(E, prev, nullptr, nullptr, nullptr, cur, E.coef));
+    for (int k = 2; k <= dA; k++) {
+      TRY(lap<float>(E, cur, prev, nullptr, nullptr, nxt, E.coef + (size_t)(k - 1) * 3 * Tn));
+      Cx<float>* t = prev;
       prev = cur;
       cur = nxt;
-      nxt = tmp;
+      nxt = t;
     }
-    // Rayleigh-Ritz on the filtered block cur: needs W (use nxt), outputs X (prev is free) and AX (W buffer)
-    double* coef_save = B.coef;
-    B.coef = B.coef + (size_t)degree * 3 * Tn;
-    dlma_status s = rayleigh_ritz(ctx, B, t0, Tn, m, n, cur, nxt, prev, B.W, nsplit);
-    // near convergence, a second Rayleigh-Ritz pass on the (now well-conditioned)
-    // block restores orthonormality lost in the one-pass Gram orthogonalisation
-    if (s == DLMA_OK && worst < 1e-6) s = rayleigh_ritz(ctx, B, t0, Tn, m, n, prev, nxt, cur, B.W, nsplit);
-    B.coef = coef_save;
-    TRY(s);
-    if (worst < 1e-6) { B.X = cur; B.Y = prev; B.Yn = nxt; }
-    else { B.X = prev; B.Y = cur; B.Yn = nxt; }
+    // cur holds the filtered block; prev and nxt are free (one of them held X)
+    TRY(rayleigh_ritz<float>(E, cur, prev, nxt, E.F3, nullptr, plain));
+    p3[0] = nxt;
+    p3[1] = cur;
+    p3[2] = prev;
   }
-  if (!conv) return set_err(ctx, DLMA_ERR_NOT_CONVERGED, "eigensolver did not reach tol %.3g in %d iterations", tol, it);
+  Cx<float>* X = p3[0];
+  // ---- phase B: FP64 Ritz vectors, FP32 residual-driven filter ----
+  Cx<double> *X64 = E.D0, *W64 = E.D1, *Y64 = E.D2;
+  k_convert_block<float, double><<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X, Y64, E.blk);
+  CHECK_LAUNCH();
+  Cx<float>* R32 = E.F3;   // residual R = AX - X Theta
+  Cx<float>* Ebuf[3];
+  {
+    int q = 0;
+    Cx<float>* all[4] = {E.F0, E.F1, E.F2, E.F3};
+    for (int i = 0; i < 4; i++)
+      if (all[i] != R32) Ebuf[q++] = all[i];
+  }
+  // Rayleigh-Ritz in FP64 on the FP32 result: X64 = Ritz vectors, Y64 = A X64, R32 = AX - X Theta
+  E.drop_rel = 1e-24;
+  TRY(rayleigh_ritz<double>(E, Y64, W64, X64, Y64, R32, plain));
+  bool conv = false;
+  int itB = 0;
+  int dB = d;
+  for (; itB < maxB; itB++) {
+    TRY(fetch<double>(E, &worst, X64));
+    if (worst <= tol) { conv = true; break; }
+    dB = safe_degree(E, 1e6, d);
+    cheb_coefficients(E, dB, hc, &hs);
+    CU(cudaMemcpyAsync(E.coef, hc.data(), sizeof(double) * ncoef, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(E.scol, hs.data(), sizeof(double) * nscol, cudaMemcpyHostToDevice, ctx->stream));
+    // E_1 = a_1 R s_0 ; E_{k+1} = a_k A E_k + b_k E_k + c_k E_{k-1} + a_k R s_k
+    Cx<float>*em = nullptr, *ec = Ebuf[0], *en = Ebuf[1], *spare = Ebuf[2];
+    TRY(lap<float>(E, nullptr, nullptr, R32, E.scol, ec, E.coef));
+    for (int k = 2; k <= dB; k++) {
+      TRY(lap<float>(E, ec, em, R32, E.scol + (size_t)(k - 1) * Tn * m, en, E.coef + (size_t)(k - 1) * 3 * Tn));
+      Cx<float>* t = em ? em : spare;
+      em = ec;
+      ec = en;
+      en = t;
+    }
+    // Y = X s_d + E_d
+    k_combine<<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X64, ec, E.scol + (size_t)dB * Tn * m,
+                                                                        (size_t)E.n * m, m, E.blk, Y64);
+    CHECK_LAUNCH();
+    // Rayleigh-Ritz of Y64: W64 = A Y64; X64 <- Y64 C; AX into W... (use X64 as output: Y64 and W64 are inputs)
+    TRY(lap<double>(E, Y64, nullptr, nullptr, nullptr, W64, plain));
+    TRY(gram<double>(E, Y64, Y64, E.G));
+    TRY(gram<double>(E, Y64, W64, E.H));
+    TRY(small_rr<double>(E));
+    TRY(rotate<double>(E, Y64, X64));
+    TRY(rotate<double>(E, W64, Y64));   // A X (Y64 is free after the rotation above)
+    k_resid<double><<<dim3((m + 31) / 32, Tn), 256, 0, ctx->stream>>>(X64, Y64, E.theta, E.n, m, E.res, R32);
+    CHECK_LAUNCH();
+  }
+  if (!conv) {
+    TRY(fetch<double>(E, &worst, X64));
+    conv = worst <= tol;
+  }
+  if (!conv)
+    return set_err(ctx, DLMA_ERR_NOT_CONVERGED, "eigensolver at %.3g, not %.3g, after %d + %d iterations", worst, tol,
+                   it, itB);
   for (int t = 0; t < Tn; t++)
-    for (int k = 0; k < N; k++) lam_out[(size_t)t * N + k] = th[(size_t)t * m + k];
-  *Xres = B.X;
+    for (int k = 0; k < N; k++) lam_out[(size_t)t * N + k] = E.th[(size_t)t * m + k];
+  *Xres = X64;
   *m_out = m;
+  if (iters_out) { iters_out[0] = it; iters_out[1] = itB; }
   return DLMA_OK;
 }
 
@@ -591,20 +706,14 @@ extern "C" dlma_status dlma_apply_laplacian(dlma_ctx* ctx, const double* in, dou
   if (!ctx->have_gauge) return set_err(ctx, DLMA_ERR_STATE, "no gauge field");
   if (!in || !out || nvec < 1) return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument");
   CU(cudaSetDevice(ctx->device));
-  size_t bytes = (size_t)nvec * ctx->g.V * 3 * 16;
+  const size_t bytes = (size_t)nvec * ctx->g.V * 3 * 16;
   const double* din;
   TRY(copy_in(ctx, WS_IN, in, bytes, mem, &din));
   double* dout = out;
   if (mem == DLMA_MEM_HOST) TRY(workT(ctx, WS_OUT, bytes / 8, &dout));
-  // lap = -A: alpha = -1
-  double* coef;
-  TRY(workT(ctx, WS_T0, (size_t)3 * ctx->g.T, &coef));
-  std::vector<double> h(3 * ctx->g.T);
-  for (int t = 0; t < ctx->g.T; t++) { h[3 * t] = -1; h[3 * t + 1] = 0; h[3 * t + 2] = 0; }
-  CU(cudaMemcpyAsync(coef, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
-  // canonical [nvec][V][3] equals the block layout with Tn = 1 per column when t0 = 0 and Tn = T
-  // (column j of timeslice t at (j T + t) 3 Vs)
-  TRY(lap_apply_batch(ctx, 0, ctx->g.T, nvec, (const double2*)din, nullptr, (double2*)dout, coef));
+  dim3 grid((ctx->g.V + 127) / 128, nvec);
+  k_lap_canonical<<<grid, 128, 0, ctx->stream>>>(ctx->g, ctx->U3, (const double2*)din, (double2*)dout, nvec);
+  CHECK_LAUNCH();
   TRY(copy_out(ctx, out, dout, bytes, mem));
   CU(cudaStreamSynchronize(ctx->stream));
   return DLMA_OK;
@@ -623,10 +732,14 @@ extern "C" dlma_status dlma_laplacian_eigs(dlma_ctx* ctx, int t, int N, double t
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   CU(cudaEventRecord(e0, ctx->stream));
-  double2* X = nullptr;
-  int m = 0;
-  TRY(eig_batch(ctx, t0, Tn, N, tol, evals, &X, &m));
-  // cache (all timeslices, [N][T][Vs][3])
+  Cx<double>* X = nullptr;
+  int m = 0, iters[2] = {0, 0};
+  dlma_status st = eig_batch(ctx, t0, Tn, N, tol, evals, &X, &m, iters);
+  if (st != DLMA_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+  }
   if (ctx->eig_N != N || !ctx->eig_V) {
     if (ctx->eig_V) cudaFree(ctx->eig_V);
     ctx->eig_V = nullptr;
@@ -636,18 +749,18 @@ extern "C" dlma_status dlma_laplacian_eigs(dlma_ctx* ctx, int t, int N, double t
     ctx->eig_have.assign(ctx->g.T, 0);
     ctx->eig_N = N;
   }
-  size_t tot = (size_t)N * Tn * n;
-  k_extract<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(X, n, Tn, N, ctx->eig_V, 1, ctx->g.T, t0);
+  const size_t tot = (size_t)N * Tn * n;
+  k_extract<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(X, n, Tn, m, N, ctx->eig_V, 1, ctx->g.T, t0);
   CHECK_LAUNCH();
   for (int tt = 0; tt < Tn; tt++) {
     ctx->eig_have[t0 + tt] = 1;
     for (int k = 0; k < N; k++) ctx->eig_lam[(size_t)(t0 + tt) * N + k] = evals[(size_t)tt * N + k];
   }
   if (evecs) {
-    size_t bytes = tot * sizeof(double2);
+    const size_t bytes = tot * sizeof(double2);
     double2* dst = (double2*)evecs;
     if (mem == DLMA_MEM_HOST) TRY(workT(ctx, WS_OUT, tot, &dst));
-    k_extract<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(X, n, Tn, N, dst, 0, ctx->g.T, t0);
+    k_extract<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(X, n, Tn, m, N, dst, 0, ctx->g.T, t0);
     CHECK_LAUNCH();
     if (mem == DLMA_MEM_HOST) TRY(copy_out(ctx, evecs, (const double*)dst, bytes, mem));
   }
@@ -656,6 +769,8 @@ extern "C" dlma_status dlma_laplacian_eigs(dlma_ctx* ctx, int t, int N, double t
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   ctx->timing[0] = ms;
+  ctx->timing[1] = iters[0];
+  ctx->timing[2] = iters[1];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return DLMA_OK;

@@ -1,0 +1,182 @@
+// Small dense Rayleigh-Ritz problems of the Laplacian eigensolver, one CTA per
+// timeslice: from G = Y^dag Y and H = Y^dag A Y (m x m, hermitian) produce C
+// such that Y C are orthonormal Ritz vectors with ascending Ritz values.
+//
+//   G = Q diag(g) Q^dag (Jacobi),  S = Q diag(g)^-1/2 (directions with tiny g dropped),
+//   S^dag H S = Z diag(theta) Z^dag (Jacobi),  C = S Z sorted by theta.
+//
+// The eigendecompositions use the parallel cyclic Jacobi method (round-robin
+// pairing, m/2 disjoint complex rotations per round).  T = float serves the
+// single-precision phase of the eigensolver, T = double its final phase, where
+// both matrices arrive nearly diagonal and Jacobi needs two or three sweeps.
+#pragma once
+#include "common.cuh"
+
+template <class T> struct SmallPrec;
+template <> struct SmallPrec<float> { static constexpr double off_tol = 1e-13; };
+template <> struct SmallPrec<double> { static constexpr double off_tol = 1e-30; };
+
+__device__ __forceinline__ int rr_pos(int idx, int r, int m) { return idx == 0 ? 0 : ((idx - 1 + r) % (m - 1)) + 1; }
+
+// Diagonalise the hermitian A [m][m] (row-major, in place), accumulating the
+// rotations into the columns of V (which holds the initial basis).
+template <class T>
+__device__ void jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, double* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int np = m / 2;
+  for (int sweep = 0; sweep < 40; sweep++) {
+    double off = 0, dia = 0;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = e / m, j = e % m;
+      const Cx<T> v = A[e];
+      if (i == j) dia += (double)v.re * v.re;
+      else off += (double)v.re * v.re + (double)v.im * v.im;
+    }
+    red[tid] = off;
+    red[nt + tid] = dia;
+    __syncthreads();
+    for (int s = nt / 2; s > 0; s >>= 1) {
+      if (tid < s) { red[tid] += red[tid + s]; red[nt + tid] += red[nt + tid + s]; }
+      __syncthreads();
+    }
+    const bool done = red[0] <= SmallPrec<T>::off_tol * red[nt] || red[0] == 0.0;
+    __syncthreads();
+    if (done) break;
+    for (int r = 0; r < m - 1; r++) {
+      for (int k = tid; k < np; k += nt) {
+        const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
+        const T a = A[p * m + p].re, d = A[q * m + q].re;
+        const Cx<T> b = A[p * m + q];
+        const T ab = sqrt(b.re * b.re + b.im * b.im);
+        if (!(ab > (T)1e-30 * (fabs(a) + fabs(d)) && ab > (T)0)) {
+          rc[k] = 1; rs[k] = 0; re[k] = cx<T>(1, 0);
+          continue;
+        }
+        const T tau = (d - a) / (2 * ab);
+        const T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt(1 + tau * tau));
+        const T c = 1 / sqrt(1 + tt * tt);
+        rc[k] = c;
+        rs[k] = tt * c;
+        re[k] = cx<T>(b.re / ab, -b.im / ab);   // e^{-i phi}
+      }
+      __syncthreads();
+      for (int e = tid; e < np * m; e += nt) {        // A <- A J, V <- V J (columns p, q)
+        const int k = e / m, i = e % m;
+        const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
+        const T c = rc[k], s = rs[k];
+        const Cx<T> ph = re[k];
+        const Cx<T> ap = A[i * m + p], aq = ph * A[i * m + q];
+        A[i * m + p] = c * ap - s * aq;
+        A[i * m + q] = s * ap + c * aq;
+        const Cx<T> vp = V[i * m + p], vq = ph * V[i * m + q];
+        V[i * m + p] = c * vp - s * vq;
+        V[i * m + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * m; e += nt) {        // A <- J^dag A (rows p, q)
+        const int k = e / m, j = e % m;
+        const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
+        const T c = rc[k], s = rs[k];
+        const Cx<T> ph = conj(re[k]);
+        const Cx<T> ap = A[p * m + j], aq = ph * A[q * m + j];
+        A[p * m + j] = c * ap - s * aq;
+        A[q * m + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_small_rr(const double2* Gall, const double2* Hall, int m, double2* Call,
+                                                  double* theta_all, Cx<T>* gwork, int use_smem, int* dropped,
+                                                  double drop_rel) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int t = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const size_t mm = (size_t)m * m;
+  Cx<T>*S, *A, *Z;
+  if (use_smem) { S = (Cx<T>*)sm_raw; A = S + mm; Z = A + mm; }
+  else { S = gwork + 3 * mm * t; A = S + mm; Z = A + mm; }
+  __shared__ T rc[128], rs[128];
+  __shared__ Cx<T> re[128];
+  __shared__ double red[512], lam[256];
+  __shared__ int order[256];
+  const double2* G = Gall + mm * t;
+  const double2* H = Hall + mm * t;
+  // 1) eigen-decomposition of the Gram matrix
+  for (size_t e = tid; e < mm; e += nt) {
+    A[e] = cx<T>((T)G[e].x, (T)G[e].y);
+    S[e] = cx<T>((e / m) == (e % m) ? (T)1 : (T)0, 0);
+  }
+  __syncthreads();
+  jacobi<T>(A, S, m, rc, rs, re, red);
+  // 2) S <- Q diag(g)^-1/2, dropping directions with g <= drop_rel gmax
+  if (tid == 0) {
+    double gmax = 0;
+    for (int i = 0; i < m; i++) gmax = fmax(gmax, (double)A[i * m + i].re);
+    red[0] = gmax;
+  }
+  __syncthreads();
+  const double gmax = red[0];
+  __syncthreads();
+  for (int i = tid; i < m; i += nt) {
+    const double gi = A[i * m + i].re;
+    lam[i] = gi > drop_rel * gmax ? 1.0 / sqrt(gi) : 0.0;
+  }
+  __syncthreads();
+  for (size_t e = tid; e < mm; e += nt) S[e] = (T)lam[e % m] * S[e];
+  __syncthreads();
+  // 3) Z <- H S ; A <- S^dag Z  (= S^dag H S)
+  for (size_t e = tid; e < mm; e += nt) {
+    const int i = e / m, j = e % m;
+    Cx<T> s = cx<T>(0, 0);
+    for (int l = 0; l < m; l++) fma_acc(s, cx<T>((T)H[i * m + l].x, (T)H[i * m + l].y), S[l * m + j]);
+    Z[e] = s;
+  }
+  __syncthreads();
+  for (size_t e = tid; e < mm; e += nt) {
+    const int i = e / m, j = e % m;
+    Cx<T> s = cx<T>(0, 0);
+    for (int l = 0; l < m; l++) fma_conj_acc(s, S[l * m + i], Z[l * m + j]);
+    A[e] = s;
+  }
+  __syncthreads();
+  for (size_t e = tid; e < mm; e += nt) {   // hermitian part (round-off)
+    const int i = e / m, j = e % m;
+    if (i < j) {
+      const Cx<T> a = A[i * m + j], b = A[j * m + i];
+      const Cx<T> h = cx<T>((T)0.5 * (a.re + b.re), (T)0.5 * (a.im - b.im));
+      A[i * m + j] = h;
+      A[j * m + i] = conj(h);
+    } else if (i == j) {
+      A[e].im = 0;
+    }
+  }
+  for (size_t e = tid; e < mm; e += nt) Z[e] = cx<T>((e / m) == (e % m) ? (T)1 : (T)0, 0);
+  __syncthreads();
+  jacobi<T>(A, Z, m, rc, rs, re, red);
+  // 4) sort ascending.  A dropped direction i has an exactly zero row and column
+  //    in S^dag H S, so Jacobi never rotates it and it keeps position i: sort it last.
+  for (int i = tid; i < m; i += nt) lam[i] = lam[i] > 0 ? (double)A[i * m + i].re : 1e300;
+  __syncthreads();
+  for (int i = tid; i < m; i += nt) {
+    int rank = 0;
+    for (int l = 0; l < m; l++) rank += (lam[l] < lam[i]) || (lam[l] == lam[i] && l < i);
+    order[rank] = i;
+  }
+  __syncthreads();
+  // 5) C = S Z[:, order]
+  double2* Cout = Call + mm * t;
+  for (size_t e = tid; e < mm; e += nt) {
+    const int i = e / m, j = e % m;
+    const int zj = order[j];
+    Cx<T> s = cx<T>(0, 0);
+    for (int l = 0; l < m; l++) fma_acc(s, S[i * m + l], Z[l * m + zj]);
+    Cout[e] = make_double2((double)s.re, (double)s.im);
+  }
+  for (int j = tid; j < m; j += nt) {
+    const double v = lam[order[j]];
+    theta_all[(size_t)t * m + j] = v;
+    if (v > 1e299) atomicAdd(dropped, 1);
+  }
+}

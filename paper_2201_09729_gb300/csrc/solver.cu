@@ -435,6 +435,7 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
     k_convert<DLMA_FP64, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.r64.data, nullptr, B.rhs.data, B.rhs.scale,
                                                          B.sc.rnorm, 1, B.sc.outer_active, nullptr);
     CHECK_LAUNCH();
+    if (outer == 0) TRY(autotune_hop(ctx, PS, B.rhs, B.tmp, B.z));   // before the graph capture
     TRY(schur_apply(ctx, B.rhs, B.tmp, B.z, 1, B.sc.outer_active, nullptr));
     k_convert<PS, PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.z.data, B.z.scale, B.rl.data, nullptr, nullptr, 0,
                                                   B.sc.outer_active, B.part2);
