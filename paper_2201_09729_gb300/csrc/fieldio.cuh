@@ -67,7 +67,9 @@ __device__ __forceinline__ void store_spinor(void* base, float* scale, int Vh, i
 #pragma unroll
     for (int k = 0; k < 12; k++)
       m = fmaxf(m, fmaxf(fabsf((float)s.c[k / 3][k % 3].re), fabsf((float)s.c[k / 3][k % 3].im)));
-    float inv = m > 0.f ? 1.f / m : 0.f;
+    // sites below 1e-30 (down to float denormals, whose reciprocal overflows) are flushed to zero
+    if (!(m > 1e-30f)) m = 0.f;
+    const float inv = m > 0.f ? 1.f / m : 0.f;
     uint4* b = (uint4*)base;
 #pragma unroll
     for (int q = 0; q < 3; q++) {

@@ -12,9 +12,12 @@
 #pragma once
 #include "common.cuh"
 
+// a pair (p, q) is rotated only if |a_pq| > eps sqrt(|a_pp a_qq|): below that the
+// entry is at the rounding level of the precision; a sweep without any rotation ends
+// the iteration (the classical threshold Jacobi method)
 template <class T> struct SmallPrec;
-template <> struct SmallPrec<float> { static constexpr double off_tol = 1e-13; };
-template <> struct SmallPrec<double> { static constexpr double off_tol = 1e-30; };
+template <> struct SmallPrec<float> { static constexpr float eps = 1e-6f; };
+template <> struct SmallPrec<double> { static constexpr double eps = 1e-15; };
 
 __device__ __forceinline__ int rr_pos(int idx, int r, int m) { return idx == 0 ? 0 : ((idx - 1 + r) % (m - 1)) + 1; }
 
@@ -24,34 +27,30 @@ template <class T>
 __device__ void jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, double* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int np = m / 2;
+  __shared__ int rotated;
+  __shared__ double dmax;
+  if (tid == 0) {
+    double mx = 0;
+    for (int i = 0; i < m; i++) mx = fmax(mx, fabs((double)A[i * m + i].re));
+    dmax = mx;
+  }
+  __syncthreads();
+  // entries below this absolute floor are rounding noise even next to tiny diagonals
+  const T floor_abs = (T)(1e-4 * (double)SmallPrec<T>::eps * dmax);
   for (int sweep = 0; sweep < 40; sweep++) {
-    double off = 0, dia = 0;
-    for (int e = tid; e < m * m; e += nt) {
-      const int i = e / m, j = e % m;
-      const Cx<T> v = A[e];
-      if (i == j) dia += (double)v.re * v.re;
-      else off += (double)v.re * v.re + (double)v.im * v.im;
-    }
-    red[tid] = off;
-    red[nt + tid] = dia;
+    if (tid == 0) rotated = 0;
     __syncthreads();
-    for (int s = nt / 2; s > 0; s >>= 1) {
-      if (tid < s) { red[tid] += red[tid + s]; red[nt + tid] += red[nt + tid + s]; }
-      __syncthreads();
-    }
-    const bool done = red[0] <= SmallPrec<T>::off_tol * red[nt] || red[0] == 0.0;
-    __syncthreads();
-    if (done) break;
     for (int r = 0; r < m - 1; r++) {
       for (int k = tid; k < np; k += nt) {
         const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
         const T a = A[p * m + p].re, d = A[q * m + q].re;
         const Cx<T> b = A[p * m + q];
         const T ab = sqrt(b.re * b.re + b.im * b.im);
-        if (!(ab > (T)1e-30 * (fabs(a) + fabs(d)) && ab > (T)0)) {
+        if (!(ab > SmallPrec<T>::eps * sqrt(fabs(a * d)) && ab > floor_abs && ab > (T)1e-300)) {
           rc[k] = 1; rs[k] = 0; re[k] = cx<T>(1, 0);
           continue;
         }
+        rotated = 1;
         const T tau = (d - a) / (2 * ab);
         const T tt = (tau >= 0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt(1 + tau * tau));
         const T c = 1 / sqrt(1 + tt * tt);
@@ -62,6 +61,7 @@ __device__ void jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, doubl
       __syncthreads();
       for (int e = tid; e < np * m; e += nt) {        // A <- A J, V <- V J (columns p, q)
         const int k = e / m, i = e % m;
+        if (rs[k] == (T)0) continue;                  // pair not rotated this round
         const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
         const T c = rc[k], s = rs[k];
         const Cx<T> ph = re[k];
@@ -75,6 +75,7 @@ __device__ void jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, doubl
       __syncthreads();
       for (int e = tid; e < np * m; e += nt) {        // A <- J^dag A (rows p, q)
         const int k = e / m, j = e % m;
+        if (rs[k] == (T)0) continue;
         const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
         const T c = rc[k], s = rs[k];
         const Cx<T> ph = conj(re[k]);
@@ -84,7 +85,10 @@ __device__ void jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, doubl
       }
       __syncthreads();
     }
+    if (!rotated) break;      // every pair below the threshold: converged
+    __syncthreads();
   }
+  (void)red;
 }
 
 template <class T>

@@ -3,12 +3,16 @@
 //
 // Even-odd Schur system Dhat x_e = bhat, bhat = b_e - D_eo T_oo^-1 b_o, solved
 // by CG on the normal equations Dhat^dag Dhat x_e = Dhat^dag bhat (CGNE).
-// Precision scheme: an FP64 outer defect-correction loop recomputes the true
-// residual r = bhat - Dhat x in double precision and restarts an inner CGNE
-// run in FP32 (or FP16 with per-site scales, FP32 vector algebra) on the
-// normalised residual; the correction is accumulated into x in FP64.  Every
-// right-hand side carries its own CG scalars on the device and is retired
-// (masked out of every kernel) once converged.  A chunk of inner iterations is
+// Precision scheme (reliable updates): the Krylov iteration runs in FP32 (or
+// FP16 with per-site scales for the stencil, FP32 vector algebra) on the system
+// scaled by s_j = |bhat_j|.  When a right-hand side's iterated residual has
+// dropped by a factor delta since its last update, it pauses; at the end of the
+// chunk its low-precision solution is folded into the FP64 solution, the true
+// Schur residual r = bhat - Dhat x is recomputed in FP64 and, unless it is below
+// the tolerance, the iterated normal-equation residual is replaced by
+// Dhat^dag r / s_j and the iteration resumes with the same search direction.
+// Every right-hand side carries its own CG scalars on the device and is retired
+// (masked out of every kernel) once converged.  A chunk of iterations is
 // captured once into a CUDA graph and replayed; the host polls one pinned
 // counter per chunk, with an iteration cap and a wall-clock limit, so a solve
 // never waits without bound.
@@ -21,77 +25,96 @@ namespace {
 constexpr int BX = 128;   // sites per block for vector kernels
 
 struct CgScal {
-  double* rr;      // current |r|^2 of the normal equations
+  double* rr;      // current |r|^2 of the (scaled) normal equations
   double* alpha;
   double* beta;
-  double* stop2;   // stopping threshold on |r|^2
-  double* rnorm;   // FP64 outer residual norm per rhs
+  double* stop2;   // |r|^2 that triggers the next reliable update
+  double* rnorm;   // FP64 Schur residual norm per rhs (at the last update)
   double* bnorm;   // |b| per rhs (full lattice)
-  int* active;     // inner-loop mask
-  int* outer_active;
-  int* iters;      // inner iterations this outer cycle
-  int* count;      // [0] number of active rhs, [1] nonfinite flag
+  double* scale;   // s_j = |bhat_j|: the low-precision system solves for x / s_j
+  double* rrnew;   // recomputed |r|^2 after an update
+  int* active;     // iterating
+  int* alive;      // not yet converged
+  int* ru;         // paused for a reliable update
+  int* upd;        // update and resume (ru and not converged)
+  int* iters;      // inner iterations in total
+  int* since;      // inner iterations since the last update
+  int* nupd;       // reliable updates
+  double* rbest;   // smallest FP64 residual seen at an update
+  int* stall;      // consecutive updates without halving rbest
+  int* rst;        // restart the search direction at this update (p = r)
+  int* count;      // [0] iterating, [1] nonfinite flag, [2] paused for update
 };
 
-// reduce per-(rhs, block) partials: out[j] = sum_b part[j * nb + b]; one warp per rhs
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ double reduce_row(const double* part, int nb, int j) {
-  double s = 0;
-  for (int b = threadIdx.x; b < nb; b += 32) s += part[(size_t)j * nb + b];
-  return __shfl_sync(0xffffffffu, warp_sum(s), 0);
-}
 
+// alpha_j = |r|^2 / |Dhat p|^2 (one warp per rhs over the stencil's partial sums)
 __global__ void k_cg_alpha(const double* part, int nb, int nrhs, CgScal sc) {
-  int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  if (j >= nrhs) return;
-  if (!sc.active[j]) return;
-  // lanes of one warp: recompute with lane index
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (j >= nrhs || !sc.active[j]) return;
+  const int lane = threadIdx.x & 31;
   double s = 0;
-  int lane = threadIdx.x & 31;
   for (int b = lane; b < nb; b += 32) s += part[(size_t)j * nb + b];
   s = warp_sum(s);
   if (lane == 0) {
-    double qq = s;
-    double a = (qq > 0 && isfinite(qq)) ? sc.rr[j] / qq : 0.0;
-    sc.alpha[j] = a;
-    if (!(qq > 0) || !isfinite(qq)) {
+    const double qq = s;
+    const double a = sc.rr[j] / qq;
+    const bool ok = qq > 0 && isfinite(qq) && isfinite(a);
+    sc.alpha[j] = ok ? a : 0.0;
+    if (!ok) {
       sc.active[j] = 0;
+      sc.ru[j] = 1;                       // hand over to the FP64 check
       if (!isfinite(qq)) sc.count[1] = 1;
     }
   }
 }
 
-__global__ void k_cg_beta(const double* part, int nb, int nrhs, CgScal sc) {
-  int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  if (j >= nrhs) return;
-  if (!sc.active[j]) return;
-  int lane = threadIdx.x & 31;
+// beta_j; pause for a reliable update when |r|^2 fell below stop2 or after max_since iterations
+__global__ void k_cg_beta(const double* part, int nb, int nrhs, CgScal sc, int max_since, double delta2) {
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (j >= nrhs || !sc.active[j]) return;
+  const int lane = threadIdx.x & 31;
   double s = 0;
   for (int b = lane; b < nb; b += 32) s += part[(size_t)j * nb + b];
   s = warp_sum(s);
   if (lane == 0) {
-    double rrn = s;
-    sc.beta[j] = rrn / sc.rr[j];
+    const double rrn = s;
+    const double bt = rrn / sc.rr[j];
+    sc.beta[j] = isfinite(bt) ? bt : 0.0;
     sc.rr[j] = rrn;
     sc.iters[j] += 1;
+    sc.since[j] += 1;
     if (!isfinite(rrn)) { sc.active[j] = 0; sc.count[1] = 1; }
-    else if (rrn <= sc.stop2[j]) sc.active[j] = 0;
+    // request a reliable update; the pause takes effect after this iteration's
+    // p update (k_pause), so the search direction stays consistent with r.  An
+    // exhausted recursion (|r| = 0 or an overflowing beta) also asks for the FP64 check.
+    else if (rrn <= sc.stop2[j] || sc.since[j] >= max_since || !(rrn > 0) || !isfinite(bt) ||
+             rrn * delta2 > 1e4 * sc.stop2[j])    // |r|^2 grew 1e4 x above its value at the last update
+      sc.ru[j] = 1;
   }
 }
 
-__global__ void k_count(const int* act, int n, int* count) {
-  __shared__ int s;
-  if (threadIdx.x == 0) s = 0;
+// apply the pauses requested in k_cg_beta once p has been updated
+__global__ void k_pause(int nrhs, CgScal sc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nrhs && sc.ru[j]) sc.active[j] = 0;
+}
+
+// count[0] = iterating rhs, count[2] = rhs paused for an update
+__global__ void k_count(const int* act, const int* ru, int n, int* count) {
+  __shared__ int s0, s2;
+  if (threadIdx.x == 0) { s0 = 0; s2 = 0; }
   __syncthreads();
-  int c = 0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) c += act[j] != 0;
-  atomicAdd(&s, c);
+  int c0 = 0, c2 = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) { c0 += act[j] != 0; c2 += ru[j] != 0; }
+  atomicAdd(&s0, c0);
+  atomicAdd(&s2, c2);
   __syncthreads();
-  if (threadIdx.x == 0) count[0] = s;
+  if (threadIdx.x == 0) { count[0] = s0; count[2] = s2; }
 }
 
 // block-level partial of a per-thread double, one entry per (rhs, block)
@@ -121,16 +144,18 @@ template <int PB, int PS>
 __global__ void __launch_bounds__(BX) k_update_xr(int Vh, int nrhs, void* x, void* r, const void* p, const void* z,
                                                    const float* zsc, CgScal sc, double* part) {
   typedef typename PT<PB>::R R;
-  int i = blockIdx.x * BX + threadIdx.x;
-  int j = blockIdx.y;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y;
+  const bool on = sc.active[j] != 0;
   double n = 0;
-  if (i < Vh && sc.active[j]) {
-    size_t sb = field_units_per_rhs(PB, Vh) * 16 * j, ss = field_units_per_rhs(PS, Vh) * 16 * j;
-    R a = (R)sc.alpha[j];
+  if (i < Vh && on) {
+    const size_t sb = field_units_per_rhs(PB, Vh) * 16 * j, ss = field_units_per_rhs(PS, Vh) * 16 * j;
+    const R a = (R)sc.alpha[j];
     Spinor<R> xv = load_spinor<PB>((char*)x + sb, nullptr, Vh, i);
     Spinor<R> rv = load_spinor<PB>((char*)r + sb, nullptr, Vh, i);
-    Spinor<R> pv = load_spinor<PB>((const char*)p + sb, nullptr, Vh, i);
-    Spinor<typename PT<PS>::R> zv = load_spinor<PS>((const char*)z + ss, zsc ? zsc + (size_t)j * Vh : nullptr, Vh, i);
+    const Spinor<R> pv = load_spinor<PB>((const char*)p + sb, nullptr, Vh, i);
+    const Spinor<typename PT<PS>::R> zv =
+        load_spinor<PS>((const char*)z + ss, zsc ? zsc + (size_t)j * Vh : nullptr, Vh, i);
 #pragma unroll
     for (int s = 0; s < 4; s++)
 #pragma unroll
@@ -142,7 +167,7 @@ __global__ void __launch_bounds__(BX) k_update_xr(int Vh, int nrhs, void* x, voi
     store_spinor<PB>((char*)r + sb, nullptr, Vh, i, rv);
     n = snorm(rv);
   }
-  block_partial(n, part, sc.active[j] ? j : nrhs, nrhs);
+  block_partial(n, part, on ? j : nrhs, nrhs);
 }
 
 // p = r + beta p  (and the stencil-precision copy when PS != PB)
@@ -150,12 +175,12 @@ template <int PB, int PS>
 __global__ void __launch_bounds__(BX) k_update_p(int Vh, int nrhs, const void* r, void* p, void* ps, float* pssc,
                                                   CgScal sc) {
   typedef typename PT<PB>::R R;
-  int i = blockIdx.x * BX + threadIdx.x;
-  int j = blockIdx.y;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y;
   if (i >= Vh || !sc.active[j]) return;
-  size_t sb = field_units_per_rhs(PB, Vh) * 16 * j;
-  R b = (R)sc.beta[j];
-  Spinor<R> rv = load_spinor<PB>((const char*)r + sb, nullptr, Vh, i);
+  const size_t sb = field_units_per_rhs(PB, Vh) * 16 * j;
+  const R b = (R)sc.beta[j];
+  const Spinor<R> rv = load_spinor<PB>((const char*)r + sb, nullptr, Vh, i);
   Spinor<R> pv = load_spinor<PB>((char*)p + sb, nullptr, Vh, i);
 #pragma unroll
   for (int s = 0; s < 4; s++)
@@ -163,7 +188,7 @@ __global__ void __launch_bounds__(BX) k_update_p(int Vh, int nrhs, const void* r
     for (int c = 0; c < 3; c++) pv.c[s][c] = rv.c[s][c] + b * pv.c[s][c];
   store_spinor<PB>((char*)p + sb, nullptr, Vh, i, pv);
   if (PS != PB) {
-    size_t ss = field_units_per_rhs(PS, Vh) * 16 * j;
+    const size_t ss = field_units_per_rhs(PS, Vh) * 16 * j;
     Spinor<typename PT<PS>::R> q;
 #pragma unroll
     for (int s = 0; s < 4; s++)
@@ -179,13 +204,14 @@ __global__ void __launch_bounds__(BX) k_convert(int Vh, int nrhs, const void* in
                                                  float* outsc, const double* f, int finv, const int* mask,
                                                  double* part) {
   typedef typename PT<PO>::R R;
-  int i = blockIdx.x * BX + threadIdx.x;
-  int j = blockIdx.y;
-  bool on = mask ? mask[j] != 0 : true;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y;
+  const bool on = mask ? mask[j] != 0 : true;
   double n = 0;
   if (i < Vh && on) {
-    size_t si = field_units_per_rhs(PI, Vh) * 16 * j, so = field_units_per_rhs(PO, Vh) * 16 * j;
-    Spinor<typename PT<PI>::R> v = load_spinor<PI>((const char*)in + si, insc ? insc + (size_t)j * Vh : nullptr, Vh, i);
+    const size_t si = field_units_per_rhs(PI, Vh) * 16 * j, so = field_units_per_rhs(PO, Vh) * 16 * j;
+    const Spinor<typename PT<PI>::R> v =
+        load_spinor<PI>((const char*)in + si, insc ? insc + (size_t)j * Vh : nullptr, Vh, i);
     double ff = 1.0;
     if (f) ff = finv ? (f[j] > 0 ? 1.0 / f[j] : 0.0) : f[j];
     Spinor<R> o;
@@ -199,16 +225,16 @@ __global__ void __launch_bounds__(BX) k_convert(int Vh, int nrhs, const void* in
   if (part) block_partial(n, part, on ? j : nrhs, nrhs);
 }
 
-// x64 += f_j * lo    (defect-correction accumulation)
+// x64 += f_j * lo; lo = 0   (reliable update: fold the low-precision solution into FP64)
 template <int PL>
-__global__ void __launch_bounds__(BX) k_accum(int Vh, int nrhs, double2* x, const void* lo, const double* f,
-                                               const int* mask) {
-  int i = blockIdx.x * BX + threadIdx.x;
-  int j = blockIdx.y;
+__global__ void __launch_bounds__(BX) k_fold(int Vh, int nrhs, double2* x, void* lo, const double* f,
+                                              const int* mask) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y;
   if (i >= Vh || !mask[j]) return;
-  size_t sl = field_units_per_rhs(PL, Vh) * 16 * j;
-  Spinor<typename PT<PL>::R> v = load_spinor<PL>((const char*)lo + sl, nullptr, Vh, i);
-  double ff = f[j];
+  const size_t sl = field_units_per_rhs(PL, Vh) * 16 * j;
+  const Spinor<typename PT<PL>::R> v = load_spinor<PL>((const char*)lo + sl, nullptr, Vh, i);
+  const double ff = f[j];
   double2* xb = x + (size_t)12 * Vh * j;
 #pragma unroll
   for (int k = 0; k < 12; k++) {
@@ -217,21 +243,27 @@ __global__ void __launch_bounds__(BX) k_accum(int Vh, int nrhs, double2* x, cons
     e.y += ff * (double)v.c[k / 3][k % 3].im;
     xb[(size_t)k * Vh + i] = e;
   }
+  Spinor<typename PT<PL>::R> z;
+#pragma unroll
+  for (int s = 0; s < 4; s++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) z.c[s][c] = cx<typename PT<PL>::R>(0, 0);
+  store_spinor<PL>((char*)lo + sl, nullptr, Vh, i, z);
 }
 
 // r = a - b (FP64) with |r|^2 partial
 __global__ void __launch_bounds__(BX) k_sub64(int Vh, int nrhs, const double2* a, const double2* b, double2* r,
                                                const int* mask, double* part) {
-  int i = blockIdx.x * BX + threadIdx.x;
-  int j = blockIdx.y;
-  bool on = mask ? mask[j] != 0 : true;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y;
+  const bool on = mask ? mask[j] != 0 : true;
   double n = 0;
   if (i < Vh && on) {
-    size_t o = (size_t)12 * Vh * j;
+    const size_t o = (size_t)12 * Vh * j;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      double2 x = a[o + (size_t)k * Vh + i], y = b[o + (size_t)k * Vh + i];
-      double2 d = make_double2(x.x - y.x, x.y - y.y);
+      const double2 x = a[o + (size_t)k * Vh + i], y = b[o + (size_t)k * Vh + i];
+      const double2 d = make_double2(x.x - y.x, x.y - y.y);
       r[o + (size_t)k * Vh + i] = d;
       n += d.x * d.x + d.y * d.y;
     }
@@ -239,36 +271,50 @@ __global__ void __launch_bounds__(BX) k_sub64(int Vh, int nrhs, const double2* a
   block_partial(n, part, on ? j : nrhs, nrhs);
 }
 
-// per-rhs totals of a partial buffer: out[j] = sum_b part[j][b]
-__global__ void k_rowsum(const double* part, int nb, int nrhs, double* out, int do_sqrt) {
-  int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  if (j >= nrhs) return;
-  int lane = threadIdx.x & 31;
+// per-rhs totals of a partial buffer: out[j] = sum_b part[j][b] (rows with mask[j] == 0 untouched)
+__global__ void k_rowsum(const double* part, int nb, int nrhs, double* out, int do_sqrt, const int* mask) {
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (j >= nrhs || (mask && !mask[j])) return;
+  const int lane = threadIdx.x & 31;
   double s = 0;
   for (int b = lane; b < nb; b += 32) s += part[(size_t)j * nb + b];
   s = warp_sum(s);
   if (lane == 0) out[j] = do_sqrt ? sqrt(s) : s;
 }
 
-// inner-cycle initialisation from the normal-equation residual r0 = |r|^2 per rhs
-__global__ void k_inner_init(int nrhs, CgScal sc, const double* rr0, double delta2) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nrhs) return;
-  if (!sc.outer_active[j]) { sc.active[j] = 0; sc.iters[j] = 0; return; }
-  int on = rr0[j] > 0 && isfinite(rr0[j]);
-  sc.active[j] = on;
-  sc.rr[j] = rr0[j];
-  sc.stop2[j] = delta2 * rr0[j];
-  sc.iters[j] = 0;
-  if (!isfinite(rr0[j])) sc.count[1] = 1;
+// after the FP64 residual of the paused rhs: retire the converged, mark the rest for resumption
+__global__ void k_ru_check(int nrhs, CgScal sc, double tol) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nrhs || !sc.ru[j]) return;
+  sc.nupd[j] += 1;
+  const double r = sc.rnorm[j];
+  if (!isfinite(r)) { sc.count[1] = 1; sc.alive[j] = 0; sc.upd[j] = 0; sc.ru[j] = 0; return; }
+  if (r <= tol * sc.bnorm[j]) { sc.alive[j] = 0; sc.upd[j] = 0; sc.ru[j] = 0; return; }
+  // stagnation at the rounding level (an unreachable tolerance): restart the search
+  // direction, and give up on this rhs after four updates without progress
+  sc.rst[j] = 0;
+  if (r < 0.5 * sc.rbest[j]) { sc.rbest[j] = r; sc.stall[j] = 0; }
+  else if (++sc.stall[j] >= 4) { sc.alive[j] = 0; sc.upd[j] = 0; sc.ru[j] = 0; return; }
+  else sc.rst[j] = 1;
+  sc.upd[j] = 1;
 }
 
-// outer convergence: rhs j done when |r_j| <= tol * |b_j|
-__global__ void k_outer_check(int nrhs, CgScal sc, double tol) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= nrhs || !sc.outer_active[j]) return;
-  if (!isfinite(sc.rnorm[j])) { sc.count[1] = 1; sc.outer_active[j] = 0; return; }
-  if (sc.rnorm[j] <= tol * sc.bnorm[j]) sc.outer_active[j] = 0;
+// resume the updated rhs with the recomputed normal-equation residual
+__global__ void k_resume(int nrhs, CgScal sc, double delta2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nrhs || !sc.upd[j]) return;
+  const double rr = sc.rrnew[j];
+  sc.upd[j] = 0;
+  sc.ru[j] = 0;
+  sc.since[j] = 0;
+  if (!(rr > 0) || !isfinite(rr)) {
+    if (!isfinite(rr)) sc.count[1] = 1;
+    sc.alive[j] = 0;
+    return;
+  }
+  sc.rr[j] = rr;
+  sc.stop2[j] = delta2 * rr;
+  sc.active[j] = 1;
 }
 
 }  // namespace
@@ -281,17 +327,18 @@ struct SolveBufs {
   CgScal sc;
 };
 
-static dlma_status rowsum(dlma_ctx* ctx, const double* part, int nb, int nrhs, double* out, int do_sqrt) {
-  k_rowsum<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(part, nb, nrhs, out, do_sqrt);
+static dlma_status rowsum(dlma_ctx* ctx, const double* part, int nb, int nrhs, double* out, int do_sqrt,
+                          const int* mask) {
+  k_rowsum<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(part, nb, nrhs, out, do_sqrt, mask);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
 
 template <int PB, int PS>
-static dlma_status inner_iteration(dlma_ctx* ctx, SolveBufs& B, int nrhs) {
+static dlma_status inner_iteration(dlma_ctx* ctx, SolveBufs& B, int nrhs, int max_since, double delta2) {
   const int Vh = ctx->g.Vh;
-  dim3 gv((Vh + BX - 1) / BX, nrhs);
-  int nbh = hop_grid_x(ctx, PS);
+  const dim3 gv((Vh + BX - 1) / BX, nrhs);
+  const int nbh = hop_grid_x(ctx, PS);
   // q = Dhat p ; |q|^2 partials
   TRY(schur_apply(ctx, B.ps, B.tmp, B.q, 0, B.sc.active, B.part));
   k_cg_alpha<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(B.part, nbh, nrhs, B.sc);
@@ -301,30 +348,68 @@ static dlma_status inner_iteration(dlma_ctx* ctx, SolveBufs& B, int nrhs) {
   k_update_xr<PB, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.xl.data, B.rl.data, B.pl.data, B.z.data, B.z.scale,
                                                   B.sc, B.part2);
   CHECK_LAUNCH();
-  k_cg_beta<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(B.part2, gv.x, nrhs, B.sc);
+  k_cg_beta<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(B.part2, gv.x, nrhs, B.sc, max_since, delta2);
   CHECK_LAUNCH();
   k_update_p<PB, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, B.pl.data, B.ps.data, B.ps.scale, B.sc);
+  CHECK_LAUNCH();
+  k_pause<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
 
-// FP64 residual r64 = bhat - Dhat x64 and its norms; outer check
-static dlma_status outer_residual(dlma_ctx* ctx, SolveBufs& B, int nrhs, double tol) {
+// Reliable update of the rhs in mask ru: x64 += s x_l, x_l = 0; r64 = bhat - Dhat x64 (FP64);
+// retire the converged ones; for the others r_l = Dhat^dag (r64 / s) and resume.
+// first: the initial update (nothing to fold); restart: also reset p = r (a plain
+// defect-correction restart, used with the FP16 stencil whose rounding makes the
+// kept search direction inconsistent with the recomputed residual)
+template <int PB, int PS>
+static dlma_status reliable_update(dlma_ctx* ctx, SolveBufs& B, int nrhs, double tol_target, double delta2,
+                                   bool first, bool restart = false) {
   const int Vh = ctx->g.Vh;
-  dim3 gv((Vh + BX - 1) / BX, nrhs);
-  TRY(schur_apply(ctx, B.x64, B.t64o, B.t64, 0, B.sc.outer_active, nullptr));
+  const dim3 gv((Vh + BX - 1) / BX, nrhs);
+  const int* ru = B.sc.ru;
+  if (!first) {
+    k_fold<PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (double2*)B.x64.data, B.xl.data, B.sc.scale, ru);
+    CHECK_LAUNCH();
+  }
+  TRY(schur_apply(ctx, B.x64, B.t64o, B.t64, 0, ru, nullptr));
   k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.bh.data, (const double2*)B.t64.data,
-                                      (double2*)B.r64.data, B.sc.outer_active, B.part2);
+                                      (double2*)B.r64.data, ru, B.part2);
   CHECK_LAUNCH();
-  TRY(rowsum(ctx, B.part2, gv.x, nrhs, B.sc.rnorm, 1));
-  k_outer_check<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc, tol);
+  TRY(rowsum(ctx, B.part2, gv.x, nrhs, B.sc.rnorm, 1, ru));
+  k_ru_check<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc, tol_target);
+  CHECK_LAUNCH();
+  const int* upd = B.sc.upd;
+  // r_l = Dhat^dag (r64 / s) in the stencil precision, then in the vector precision
+  k_convert<DLMA_FP64, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.r64.data, nullptr, B.rhs.data, B.rhs.scale,
+                                                       B.sc.scale, 1, upd, nullptr);
+  CHECK_LAUNCH();
+  TRY(schur_apply(ctx, B.rhs, B.tmp, B.z, 1, upd, nullptr));
+  k_convert<PS, PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.z.data, B.z.scale, B.rl.data, nullptr, nullptr, 0, upd,
+                                                B.part2);
+  CHECK_LAUNCH();
+  TRY(rowsum(ctx, B.part2, gv.x, nrhs, B.sc.rrnew, 0, upd));
+  {
+    // p = r_l (and its stencil-precision copy): for every updated rhs on the first
+    // update or when restarting, otherwise only for the stagnating ones
+    const int* pm = (first || restart) ? upd : B.sc.rst;
+    k_convert<PB, PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, nullptr, B.pl.data, nullptr, nullptr, 0, pm,
+                                                  nullptr);
+    CHECK_LAUNCH();
+    if (PS != PB) {
+      k_convert<PB, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, nullptr, B.ps.data, B.ps.scale, nullptr, 0,
+                                                    pm, nullptr);
+      CHECK_LAUNCH();
+    }
+  }
+  k_resume<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc, delta2);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
 
 template <int PB, int PS>
 static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol,
-                               dlma_solve_info* info, double delta, int max_inner, int max_outer) {
+                               dlma_solve_info* info, double delta, int max_inner, int max_since) {
   const int Vh = ctx->g.Vh;
   SolveBufs B;
   TRY(field_alloc(ctx, WS_SOLVE_B, DLMA_FP64, 2 * nrhs, &B.b_e));
@@ -347,61 +432,48 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   TRY(field_alloc(ctx, WS_CG_Z, PS, nrhs, &B.z));
   TRY(field_alloc(ctx, WS_CG_TMP, PS, nrhs, &B.tmp));
   TRY(field_alloc(ctx, WS_CG_RHS, PS, nrhs, &B.rhs));
-  int nbmax = (Vh + 31) / 32 + 8;
+  const int nbmax = (Vh + 31) / 32 + 8;
   TRY(workT(ctx, WS_PART, (size_t)2 * nbmax * nrhs, &B.part));
   B.part2 = B.part + (size_t)nbmax * nrhs;
   double* sd;
-  TRY(workT(ctx, WS_SCAL, (size_t)8 * nrhs + 64, &sd));
+  TRY(workT(ctx, WS_SCAL, (size_t)10 * nrhs + 64, &sd));
   B.sc.rr = sd;
   B.sc.alpha = sd + nrhs;
   B.sc.beta = sd + 2 * nrhs;
   B.sc.stop2 = sd + 3 * nrhs;
   B.sc.rnorm = sd + 4 * nrhs;
   B.sc.bnorm = sd + 5 * nrhs;
-  double* rr0 = sd + 6 * nrhs;
+  B.sc.scale = sd + 6 * nrhs;
+  B.sc.rrnew = sd + 7 * nrhs;
+  double* tmpd = sd + 8 * nrhs;     // 2 nrhs scratch
+  TRY(workT(ctx, WS_T0, (size_t)nrhs + 16, &B.sc.rbest));
   int* si;
-  TRY(workT(ctx, WS_ACT, (size_t)3 * nrhs + 16, &si));
+  TRY(workT(ctx, WS_ACT, (size_t)10 * nrhs + 16, &si));
   B.sc.active = si;
-  B.sc.outer_active = si + nrhs;
-  B.sc.iters = si + 2 * nrhs;
-  B.sc.count = si + 3 * nrhs;
+  B.sc.alive = si + nrhs;
+  B.sc.ru = si + 2 * nrhs;
+  B.sc.upd = si + 3 * nrhs;
+  B.sc.iters = si + 4 * nrhs;
+  B.sc.since = si + 5 * nrhs;
+  B.sc.nupd = si + 6 * nrhs;
+  B.sc.stall = si + 7 * nrhs;
+  B.sc.rst = si + 8 * nrhs;
+  B.sc.count = si + 9 * nrhs;
   int* hcount = (int*)ctx->pinned;
-  std::vector<int> iters_total(nrhs, 0);
 
-  dim3 gv((Vh + BX - 1) / BX, nrhs);
-  // sources
+  const dim3 gv((Vh + BX - 1) / BX, nrhs);
   TRY(pack_parity(ctx, b_dev, 1, 0, B.b_e));
   TRY(pack_parity(ctx, b_dev, 1, 1, B.b_o));
   // |b|^2 over both parities
   k_convert<DLMA_FP64, DLMA_FP64><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.b_e.data, nullptr, B.t64.data, nullptr,
                                                               nullptr, 0, nullptr, B.part);
   CHECK_LAUNCH();
+  TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd, 0, nullptr));
   k_convert<DLMA_FP64, DLMA_FP64><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.b_o.data, nullptr, B.t64o.data, nullptr,
-                                                              nullptr, 0, nullptr, B.part + (size_t)gv.x * nrhs);
+                                                              nullptr, 0, nullptr, B.part);
   CHECK_LAUNCH();
-  // sum the two parity halves: treat as 2*nb partial columns per rhs
-  {
-    // rearrange: rows j have gv.x entries in each half; sum both halves
-    TRY(rowsum(ctx, B.part, gv.x, nrhs, rr0, 0));
-    TRY(rowsum(ctx, B.part + (size_t)gv.x * nrhs, gv.x, nrhs, B.sc.rnorm, 0));
-  }
-  std::vector<double> hb(2 * nrhs);
-  CU(cudaMemcpyAsync(hb.data(), rr0, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaMemcpyAsync(hb.data() + nrhs, B.sc.rnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
-  std::vector<double> bn(nrhs);
-  std::vector<int> act0(nrhs);
-  bool nonfinite_src = false;
-  for (int j = 0; j < nrhs; j++) {
-    bn[j] = sqrt(hb[j] + hb[nrhs + j]);
-    if (!isfinite(bn[j])) nonfinite_src = true;
-    act0[j] = bn[j] > 0 && isfinite(bn[j]);
-  }
-  if (nonfinite_src) return set_err(ctx, DLMA_ERR_NONFINITE, "a source holds NaN or Inf");
-  CU(cudaMemcpyAsync(B.sc.bnorm, bn.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
-  CU(cudaMemcpyAsync(B.sc.outer_active, act0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
-  CU(cudaMemsetAsync(B.sc.count, 0, 2 * sizeof(int), ctx->stream));
-  // bhat = b_e - D_eo T_oo^-1 b_o
+  TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd + nrhs, 0, nullptr));
+  // bhat = b_e - D_eo T_oo^-1 b_o and |bhat|
   {
     HopOp a;
     a.p_out = 1; a.hop = 0; a.own = 1; a.kout = 3;
@@ -410,59 +482,83 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
     b.p_out = 0; b.own = 1; b.kout = 0; b.s = -1.0;
     TRY(launch_hop(ctx, b, B.t64o, &B.b_e, B.bh));
   }
+  k_convert<DLMA_FP64, DLMA_FP64><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.bh.data, nullptr, B.t64.data, nullptr,
+                                                              nullptr, 0, nullptr, B.part);
+  CHECK_LAUNCH();
+  TRY(rowsum(ctx, B.part, gv.x, nrhs, B.sc.scale, 1, nullptr));
+  std::vector<double> hb(2 * nrhs), hs(nrhs);
+  CU(cudaMemcpyAsync(hb.data(), tmpd, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(hs.data(), B.sc.scale, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  std::vector<double> bn(nrhs);
+  std::vector<int> alive0(nrhs), zeros(nrhs, 0);
+  for (int j = 0; j < nrhs; j++) {
+    bn[j] = sqrt(hb[j] + hb[nrhs + j]);
+    if (!isfinite(bn[j]) || !isfinite(hs[j])) return set_err(ctx, DLMA_ERR_NONFINITE, "a source holds NaN or Inf");
+    alive0[j] = bn[j] > 0 && hs[j] > 0;
+  }
+  CU(cudaMemcpyAsync(B.sc.bnorm, bn.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemcpyAsync(B.sc.alive, alive0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemcpyAsync(B.sc.ru, alive0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+  for (int* z : {B.sc.active, B.sc.upd, B.sc.iters, B.sc.since, B.sc.nupd, B.sc.stall, B.sc.rst})
+    CU(cudaMemcpyAsync(z, zeros.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<double> big(nrhs, 1e300);
+  CU(cudaMemcpyAsync(B.sc.rbest, big.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemsetAsync(B.sc.count, 0, 4 * sizeof(int), ctx->stream));
   CU(cudaMemsetAsync(B.x64.data, 0, field_bytes_per_rhs(DLMA_FP64, Vh) * nrhs, ctx->stream));
+  CU(cudaMemsetAsync(B.xl.data, 0, field_bytes_per_rhs(PB, Vh) * nrhs, ctx->stream));
   const double tol_target = 0.5 * tol;
   const double delta2 = delta * delta;
   const int chunk = 8;
-  auto t_start = std::chrono::steady_clock::now();
+  const auto t_start = std::chrono::steady_clock::now();
   const double wall_limit_s = 600.0;
 
-  // inner CG graph (captured on first use)
+  // the first "update" sets r_l = Dhat^dag (bhat / s) and p = r_l
+  {
+    // pack one full-batch right-hand side for the block-shape autotuner before any capture
+    k_convert<DLMA_FP64, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.bh.data, nullptr, B.rhs.data, B.rhs.scale,
+                                                         B.sc.scale, 1, nullptr, nullptr);
+    CHECK_LAUNCH();
+    TRY(autotune_hop(ctx, PS, B.rhs, B.tmp, B.z));
+  }
+  TRY((reliable_update<PB, PS>(ctx, B, nrhs, tol_target, delta2, true)));
+
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   uint64_t graph_kernels = 0;
   dlma_status st = DLMA_OK;
-  int outer = 0;
-  for (; outer < max_outer; outer++) {
-    TRY(outer_residual(ctx, B, nrhs, tol_target));
-    k_count<<<1, 256, 0, ctx->stream>>>(B.sc.outer_active, nrhs, B.sc.count);
-    CHECK_LAUNCH();
-    CU(cudaMemcpyAsync(hcount, B.sc.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    if (hcount[1]) { st = set_err(ctx, DLMA_ERR_NONFINITE, "non-finite residual in the solve"); break; }
-    if (hcount[0] == 0) break;
-    // inner cycle: rhs = r64 / |r64| in stencil precision; r_l = Dhat^dag rhs
-    k_convert<DLMA_FP64, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.r64.data, nullptr, B.rhs.data, B.rhs.scale,
-                                                         B.sc.rnorm, 1, B.sc.outer_active, nullptr);
-    CHECK_LAUNCH();
-    if (outer == 0) TRY(autotune_hop(ctx, PS, B.rhs, B.tmp, B.z));   // before the graph capture
-    TRY(schur_apply(ctx, B.rhs, B.tmp, B.z, 1, B.sc.outer_active, nullptr));
-    k_convert<PS, PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.z.data, B.z.scale, B.rl.data, nullptr, nullptr, 0,
-                                                  B.sc.outer_active, B.part2);
-    CHECK_LAUNCH();
-    TRY(rowsum(ctx, B.part2, gv.x, nrhs, rr0, 0));
-    k_convert<PB, PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, nullptr, B.pl.data, nullptr, nullptr, 0,
-                                                  B.sc.outer_active, nullptr);
-    CHECK_LAUNCH();
-    if (PS != PB) {
-      k_convert<PB, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, nullptr, B.ps.data, B.ps.scale, nullptr, 0,
-                                                    B.sc.outer_active, nullptr);
-      CHECK_LAUNCH();
-    }
-    CU(cudaMemsetAsync(B.xl.data, 0, field_bytes_per_rhs(PB, Vh) * nrhs, ctx->stream));
-    k_inner_init<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc, rr0, delta2);
-    CHECK_LAUNCH();
+  int it = 0;
+  // DLMA_DEBUG_SOLVE=1: print the per-rhs solver state of the first right-hand sides
+  const bool dbg = getenv("DLMA_DEBUG_SOLVE") != nullptr;
+  auto dump = [&](const char* where) {
+    const int n = std::min(nrhs, 3);
+    std::vector<double> rr(n), rn(n), al(n), sp(n);
+    std::vector<int> ac(n), av(n), r_(n), itv(n);
+    cudaMemcpy(rr.data(), B.sc.rr, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(rn.data(), B.sc.rnorm, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(al.data(), B.sc.alpha, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(sp.data(), B.sc.stop2, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(ac.data(), B.sc.active, sizeof(int) * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(av.data(), B.sc.alive, sizeof(int) * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(r_.data(), B.sc.ru, sizeof(int) * n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(itv.data(), B.sc.iters, sizeof(int) * n, cudaMemcpyDeviceToHost);
+    for (int j = 0; j < n; j++)
+      fprintf(stderr, "[solve %s] j=%d it=%d rr=%.3e stop2=%.3e alpha=%.3e rnorm=%.3e active=%d alive=%d ru=%d\n",
+              where, j, itv[j], rr[j], sp[j], al[j], rn[j], ac[j], av[j], r_[j]);
+  };
+  if (dbg) dump("start");
+  while (true) {
     if (!gexec) {
-      uint64_t l0 = ctx->launches;
+      const uint64_t l0 = ctx->launches;
       CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
       dlma_status cs = DLMA_OK;
-      for (int k = 0; k < chunk && cs == DLMA_OK; k++) cs = inner_iteration<PB, PS>(ctx, B, nrhs);
+      for (int k = 0; k < chunk && cs == DLMA_OK; k++) cs = inner_iteration<PB, PS>(ctx, B, nrhs, max_since, delta2);
       if (cs == DLMA_OK) {
-        k_count<<<1, 256, 0, ctx->stream>>>(B.sc.active, nrhs, B.sc.count);
+        k_count<<<1, 256, 0, ctx->stream>>>(B.sc.active, B.sc.ru, nrhs, B.sc.count);
         ctx->launches++;
       }
-      cudaError_t ce = cudaMemcpyAsync(hcount, B.sc.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-      cudaError_t ee = cudaStreamEndCapture(ctx->stream, &graph);
+      const cudaError_t ce = cudaMemcpyAsync(hcount, B.sc.count, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+      const cudaError_t ee = cudaStreamEndCapture(ctx->stream, &graph);
       if (cs != DLMA_OK) return cs;
       if (ce != cudaSuccess || ee != cudaSuccess)
         return set_err(ctx, DLMA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ee != cudaSuccess ? ee : ce));
@@ -470,30 +566,32 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
       graph_kernels = ctx->launches - l0;
       ctx->launches = l0;
     }
-    int it = 0;
-    while (it < max_inner) {
-      CU(cudaGraphLaunch(gexec, ctx->stream));
-      ctx->launches += graph_kernels;
-      it += chunk;
-      CU(cudaStreamSynchronize(ctx->stream));
-      if (hcount[1] || hcount[0] == 0) break;
-      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-      if (el > wall_limit_s) { st = set_err(ctx, DLMA_ERR_TIMEOUT, "solve exceeded %.0f s", wall_limit_s); break; }
-    }
-    if (st != DLMA_OK) break;
-    if (hcount[1]) { st = set_err(ctx, DLMA_ERR_NONFINITE, "non-finite value in the inner solve"); break; }
-    // x64 += |r| * x_l
-    k_accum<PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (double2*)B.x64.data, B.xl.data, B.sc.rnorm,
-                                            B.sc.outer_active);
-    CHECK_LAUNCH();
-    std::vector<int> hit(nrhs);
-    CU(cudaMemcpyAsync(hit.data(), B.sc.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaGraphLaunch(gexec, ctx->stream));
+    ctx->launches += graph_kernels;
+    it += chunk;
     CU(cudaStreamSynchronize(ctx->stream));
-    for (int j = 0; j < nrhs; j++) iters_total[j] += hit[j];
+    if (dbg) dump("chunk");
+    if (hcount[1]) { st = set_err(ctx, DLMA_ERR_NONFINITE, "non-finite value in the solve"); break; }
+    if (hcount[2] > 0) TRY((reliable_update<PB, PS>(ctx, B, nrhs, tol_target, delta2, false, PS == DLMA_FP16S)));
+    if (dbg && hcount[2] > 0) dump("update");
+    k_count<<<1, 256, 0, ctx->stream>>>(B.sc.active, B.sc.ru, nrhs, B.sc.count);
+    CHECK_LAUNCH();
+    CU(cudaMemcpyAsync(hcount, B.sc.count, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (hcount[1]) { st = set_err(ctx, DLMA_ERR_NONFINITE, "non-finite value in the solve"); break; }
+    if (hcount[0] == 0 && hcount[2] == 0) break;
+    if (it >= max_inner) { st = set_err(ctx, DLMA_ERR_NOT_CONVERGED, "iteration cap %d reached", max_inner); break; }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (el > wall_limit_s) { st = set_err(ctx, DLMA_ERR_TIMEOUT, "solve exceeded %.0f s", wall_limit_s); break; }
   }
   if (gexec) cudaGraphExecDestroy(gexec);
   if (graph) cudaGraphDestroy(graph);
-  if (st != DLMA_OK && st != DLMA_ERR_NOT_CONVERGED) return st;
+  if (st != DLMA_OK && st != DLMA_ERR_NOT_CONVERGED && st != DLMA_ERR_TIMEOUT) return st;
+  // fold what is left of the low-precision solutions of unconverged rhs
+  if (st != DLMA_OK) {
+    k_fold<PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (double2*)B.x64.data, B.xl.data, B.sc.scale, B.sc.alive);
+    CHECK_LAUNCH();
+  }
   // x_o = T_oo^-1 (b_o - D_oe x_e)
   {
     HopOp r;
@@ -504,7 +602,7 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   TRY(unpack_parity(ctx, B.t64o, 1, 1, x_dev));
   // true residual ||b - D x|| / ||b|| on the full lattice in FP64
   {
-    Field xe = B.r64;   // reuse: x_e in r64, x_o in t64o already
+    Field xe = B.r64;
     CU(cudaMemcpyAsync(xe.data, B.x64.data, field_bytes_per_rhs(DLMA_FP64, Vh) * nrhs, cudaMemcpyDeviceToDevice,
                        ctx->stream));
     HopOp d;
@@ -513,25 +611,27 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
     k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.b_e.data, (const double2*)B.t64.data,
                                         (double2*)B.bh.data, nullptr, B.part);
     CHECK_LAUNCH();
-    TRY(rowsum(ctx, B.part, gv.x, nrhs, rr0, 0));
+    TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd, 0, nullptr));
     d.p_out = 1;
     TRY(launch_hop(ctx, d, xe, &B.t64o, B.t64));            // (Dx)_o
     k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.b_o.data, (const double2*)B.t64.data,
                                         (double2*)B.bh.data, nullptr, B.part);
     CHECK_LAUNCH();
-    TRY(rowsum(ctx, B.part, gv.x, nrhs, B.sc.rnorm, 0));
+    TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd + nrhs, 0, nullptr));
     std::vector<double> h(2 * nrhs);
-    CU(cudaMemcpyAsync(h.data(), rr0, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(h.data() + nrhs, B.sc.rnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<int> hit(nrhs), hup(nrhs);
+    CU(cudaMemcpyAsync(h.data(), tmpd, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(hit.data(), B.sc.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(hup.data(), B.sc.nupd, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     bool all = true;
     for (int j = 0; j < nrhs; j++) {
-      double res = bn[j] > 0 ? sqrt(h[j] + h[nrhs + j]) / bn[j] : 0.0;
-      int conv = res <= tol;
+      const double res = bn[j] > 0 ? sqrt(h[j] + h[nrhs + j]) / bn[j] : 0.0;
+      const int conv = res <= tol;
       all = all && conv;
       if (info) {
-        info[j].iters_inner = iters_total[j];
-        info[j].iters_outer = outer;
+        info[j].iters_inner = hit[j];
+        info[j].iters_outer = hup[j];
         info[j].true_resid = res;
         info[j].converged = conv;
       }
@@ -546,24 +646,25 @@ dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int 
   // batch size bounded by the memory cap (or 85% of free memory)
   const size_t Vh = ctx->g.Vh;
   size_t per_rhs = field_bytes_per_rhs(DLMA_FP64, Vh) * 7;
-  int pb = inner == DLMA_FP64 ? DLMA_FP64 : DLMA_FP32;
+  const int pb = inner == DLMA_FP64 ? DLMA_FP64 : DLMA_FP32;
   per_rhs += field_bytes_per_rhs(pb, Vh) * 3 + field_bytes_per_rhs(inner, Vh) * 5;
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
   size_t budget = (size_t)(0.85 * (double)(freeb + ctx->work_bytes));
   if (ctx->memcap) budget = ctx->memcap;
-  int nb = (int)std::min<size_t>((size_t)nrhs, budget / per_rhs);
+  const int nb = (int)std::min<size_t>((size_t)nrhs, budget / per_rhs);
   if (nb < 1) return set_err(ctx, DLMA_ERR_OOM, "one right-hand side needs %zu bytes", per_rhs);
   dlma_status worst = DLMA_OK;
   for (int j0 = 0; j0 < nrhs; j0 += nb) {
-    int n = std::min(nb, nrhs - j0);
+    const int n = std::min(nb, nrhs - j0);
     const double* b = b_dev + (size_t)j0 * ctx->g.V * 24;
     double* x = x_dev + (size_t)j0 * ctx->g.V * 24;
     dlma_solve_info* inf = info ? info + j0 : nullptr;
     dlma_status s;
-    if (inner == DLMA_FP64) s = solve_batch<DLMA_FP64, DLMA_FP64>(ctx, b, x, n, tol, inf, 0.1 * tol, 200000, 20);
-    else if (inner == DLMA_FP32) s = solve_batch<DLMA_FP32, DLMA_FP32>(ctx, b, x, n, tol, inf, 1e-5, 20000, 40);
-    else s = solve_batch<DLMA_FP32, DLMA_FP16S>(ctx, b, x, n, tol, inf, 3e-3, 20000, 60);
+    // delta: reduction of the iterated residual between FP64 reliable updates
+    if (inner == DLMA_FP64) s = solve_batch<DLMA_FP64, DLMA_FP64>(ctx, b, x, n, tol, inf, 1e-6, 200000, 100000);
+    else if (inner == DLMA_FP32) s = solve_batch<DLMA_FP32, DLMA_FP32>(ctx, b, x, n, tol, inf, 3e-4, 40000, 400);
+    else s = solve_batch<DLMA_FP32, DLMA_FP16S>(ctx, b, x, n, tol, inf, 3e-3, 40000, 400);
     if (s != DLMA_OK && s != DLMA_ERR_NOT_CONVERGED) return s;
     if (s != DLMA_OK) worst = s;
   }
@@ -577,7 +678,7 @@ extern "C" dlma_status dlma_solve(dlma_ctx* ctx, const double* b, double* x, int
   if (!b || !x || nrhs < 1 || !(tol > 0) || inner < DLMA_FP64 || inner > DLMA_FP16S)
     return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_solve");
   CU(cudaSetDevice(ctx->device));
-  size_t bytes = (size_t)nrhs * ctx->g.V * 12 * 16;
+  const size_t bytes = (size_t)nrhs * ctx->g.V * 12 * 16;
   const double* db;
   TRY(copy_in(ctx, WS_SRC, b, bytes, mem, &db));
   double* dx = x;
@@ -586,10 +687,10 @@ extern "C" dlma_status dlma_solve(dlma_ctx* ctx, const double* b, double* x, int
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   CU(cudaEventRecord(e0, ctx->stream));
-  dlma_status s = solve_fields(ctx, db, dx, nrhs, tol, inner, info);
+  const dlma_status s = solve_fields(ctx, db, dx, nrhs, tol, inner, info);
   CU(cudaEventRecord(e1, ctx->stream));
   if (s == DLMA_OK || s == DLMA_ERR_NOT_CONVERGED) {
-    dlma_status c = copy_out(ctx, x, dx, bytes, mem);
+    const dlma_status c = copy_out(ctx, x, dx, bytes, mem);
     if (c != DLMA_OK) return c;
   }
   CU(cudaStreamSynchronize(ctx->stream));
