@@ -93,6 +93,7 @@ struct dlma_ctx {
   double timing[3] = {0, 0, 0};
   // stencil block shape (sites x right-hand sides) per precision, chosen by autotune_hop
   int hop_sx[3] = {64, 64, 64}, hop_sy[3] = {4, 4, 4}, hop_tuned[3] = {0, 0, 0};
+  int hop_l18[3] = {0, 0, 0};   // FP32: read 18-real links instead of rebuilding row 2
 
   bool have_gauge = false, have_params = false;
   double m0 = 0, csw = 0;
@@ -101,6 +102,7 @@ struct dlma_ctx {
   double2* Ucan = nullptr;  // [V][4][3][3] canonical copy (clover build)
   double2* U64 = nullptr;   // [2][4][9][Vh]
   float4* U32 = nullptr;    // [2][4][3][Vh]  rows 0, 1 (12 reals)
+  float4* U32f = nullptr;   // [2][4][5][Vh]  all 9 entries (18 reals + 2 pad): no reconstruction
   uint4* U16a = nullptr;    // [2][4][Vh]     halves 0..7 of rows 0, 1
   uint2* U16b = nullptr;    // [2][4][Vh]     halves 8..11
   double2* U3 = nullptr;    // [3][9][V]      spatial links, lexicographic, for the Laplacian

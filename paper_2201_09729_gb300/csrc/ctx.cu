@@ -115,7 +115,7 @@ __device__ __forceinline__ M3<double> load_can(const double2* U, int s, int mu) 
 
 // ---------------------------------------------------------------------------
 // gauge conversion: canonical [V][4][3][3] -> even-odd SoA copies
-__global__ void k_gauge_convert(Geom g, const double2* __restrict__ Ucan, double2* U64, float4* U32,
+__global__ void k_gauge_convert(Geom g, const double2* __restrict__ Ucan, double2* U64, float4* U32, float4* U32f,
                                 uint4* U16a, uint2* U16b, double2* U3, float4* U3f, int* flag) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
@@ -136,6 +136,10 @@ __global__ void k_gauge_convert(Geom g, const double2* __restrict__ Ucan, double
     for (int q = 0; q < 3; q++)
       U32[(base * 3 + q) * g.Vh + i] = make_float4((float)e[2 * q].x, (float)e[2 * q].y,
                                                    (float)e[2 * q + 1].x, (float)e[2 * q + 1].y);
+    for (int q = 0; q < 5; q++) {
+      const double2 a = e[2 * q], b = 2 * q + 1 < 9 ? e[2 * q + 1] : make_double2(0, 0);
+      U32f[(base * 5 + q) * g.Vh + i] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    }
     __half2 h[6];
     for (int k = 0; k < 6; k++) h[k] = __floats2half2_rn((float)e[k].x, (float)e[k].y);
     uint4 a;
@@ -382,7 +386,7 @@ __global__ void k_index_tables(Geom g, const int4* tab, int* eo_index, int* nbr)
 // ---------------------------------------------------------------------------
 // C ABI
 static void free_all(dlma_ctx* ctx) {
-  void* ptrs[] = {ctx->nbr_tab, ctx->Ucan, ctx->U64, ctx->U32, ctx->U16a, ctx->U16b, ctx->U3, ctx->U3f, ctx->C64, ctx->Ci64,
+  void* ptrs[] = {ctx->nbr_tab, ctx->Ucan, ctx->U64, ctx->U32, ctx->U32f, ctx->U16a, ctx->U16b, ctx->U3, ctx->U3f, ctx->C64, ctx->Ci64,
                   ctx->C32, ctx->Ci32, ctx->C16, ctx->Ci16, ctx->flag, ctx->eig_V};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -427,6 +431,7 @@ extern "C" dlma_status dlma_create(const dlma_lattice* lat, int device, void* cu
   bool ok = cudaMalloc(&ctx->Ucan, 4 * 9 * V * sizeof(double2)) == cudaSuccess &&
             cudaMalloc(&ctx->U64, 2 * 4 * 9 * Vh * sizeof(double2)) == cudaSuccess &&
             cudaMalloc(&ctx->U32, 2 * 4 * 3 * Vh * sizeof(float4)) == cudaSuccess &&
+            cudaMalloc(&ctx->U32f, 2 * 4 * 5 * Vh * sizeof(float4)) == cudaSuccess &&
             cudaMalloc(&ctx->U16a, 2 * 4 * Vh * sizeof(uint4)) == cudaSuccess &&
             cudaMalloc(&ctx->U16b, 2 * 4 * Vh * sizeof(uint2)) == cudaSuccess &&
             cudaMalloc(&ctx->U3, 3 * 9 * V * sizeof(double2)) == cudaSuccess &&
@@ -493,8 +498,8 @@ extern "C" dlma_status dlma_set_gauge(dlma_ctx* ctx, const double* links, dlma_m
   CU(cudaMemcpyAsync(Ucan, dU, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   CU(cudaMemsetAsync(ctx->flag, 0, 16 * sizeof(int), ctx->stream));
   int nb = (ctx->g.V + 255) / 256;
-  k_gauge_convert<<<nb, 256, 0, ctx->stream>>>(ctx->g, Ucan, ctx->U64, ctx->U32, ctx->U16a, ctx->U16b, ctx->U3,
-                                               ctx->U3f, ctx->flag);
+  k_gauge_convert<<<nb, 256, 0, ctx->stream>>>(ctx->g, Ucan, ctx->U64, ctx->U32, ctx->U32f, ctx->U16a, ctx->U16b,
+                                               ctx->U3, ctx->U3f, ctx->flag);
   CHECK_LAUNCH();
   int h = 0;
   CU(cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

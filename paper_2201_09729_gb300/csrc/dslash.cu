@@ -18,9 +18,19 @@
 // link U_mu(x) for x of parity p at compressed index i
 template <int P>
 __device__ __forceinline__ void load_link(const void* __restrict__ Ua, const void* __restrict__ Ub, int p, int mu,
-                                          int i, int Vh, Cx<typename PT<P>::R> U[3][3]) {
+                                          int i, int Vh, Cx<typename PT<P>::R> U[3][3], bool l18) {
   typedef typename PT<P>::R R;
   size_t base = (size_t)(p * 4 + mu);
+  if (P == DLMA_FP32 && l18) {   // all 18 reals stored: no reconstruction
+    const float4* u = (const float4*)Ua;
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+      float4 v = __ldg(u + (base * 5 + q) * Vh + i);
+      U[(2 * q) / 3][(2 * q) % 3] = cx<R>(v.x, v.y);
+      if (2 * q + 1 < 9) U[(2 * q + 1) / 3][(2 * q + 1) % 3] = cx<R>(v.z, v.w);
+    }
+    return;
+  }
   if (P == DLMA_FP64) {
     const double2* u = (const double2*)Ua;
 #pragma unroll
@@ -134,6 +144,7 @@ struct HopArgs {
   double* norm_part;
   const int* active;
   const int4* nbr;    // neighbour table (dlma_ctx::nbr_tab)
+  int l18;            // FP32: Ua holds 18-real links
 };
 
 template <class R>
@@ -158,7 +169,7 @@ __device__ __forceinline__ void su3_dag_mul(const Cx<R> U[3][3], const Cx<R> h[3
   }
 }
 
-template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM>
+template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM, bool L18>
 __global__ void __launch_bounds__(256, P == DLMA_FP64 ? 2 : 3) k_hop(HopArgs a) {
   typedef typename PT<P>::R R;
   // grid x runs over right-hand-side groups (fast), grid y over site tiles: all
@@ -196,7 +207,7 @@ __global__ void __launch_bounds__(256, P == DLMA_FP64 ? 2 : 3) k_hop(HopArgs a) 
           }
           Cx<R> U[3][3];
           // forward: U_mu(x) at this site; backward: U_mu(x - mu) at the neighbour
-          load_link<P>(a.Ua, a.Ub, dir == 0 ? a.p_out : 1 - a.p_out, mu, dir == 0 ? i : n, g.Vh, U);
+          load_link<P>(a.Ua, a.Ub, dir == 0 ? a.p_out : 1 - a.p_out, mu, dir == 0 ? i : n, g.Vh, U, L18);
           const R ph = raw < 0 ? (R)-1 : (R)1;    // antiperiodic time phase (bit 31)
           Cx<R> h0[3], h1[3], w0[3], w1[3];
 #pragma unroll
@@ -295,10 +306,10 @@ int hop_grid_x(dlma_ctx* ctx, int prec) {
   return (ctx->g.Vh + sx - 1) / sx;
 }
 
-template <int P>
+template <int P, bool L18>
 static void dispatch(const HopOp& op, dim3 grid, dim3 blk, cudaStream_t st, const HopArgs& a) {
   const bool norm = op.norm_part != nullptr;
-#define L(G5I, G5H, OWN, KO, HOP, NRM) k_hop<P, G5I, G5H, OWN, KO, HOP, NRM><<<grid, blk, 0, st>>>(a)
+#define L(G5I, G5H, OWN, KO, HOP, NRM) k_hop<P, G5I, G5H, OWN, KO, HOP, NRM, L18><<<grid, blk, 0, st>>>(a)
   if (!op.hop) {                                   // Kout * (Kown * own)
     if (op.own == 1 && op.kout) L(false, false, 1, true, false, false);
     else if (op.own == 2 && !op.kout) L(false, false, 2, false, false, false);
@@ -342,6 +353,7 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   a.norm_part = op.norm_part;
   a.active = op.active;
   a.nbr = ctx->nbr_tab;
+  a.l18 = 0;
   const size_t Vh = ctx->g.Vh;
   const int p = op.p_out;
   const void* Kown = nullptr;
@@ -351,7 +363,9 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
     Kown = op.own == 3 ? (const void*)(ctx->Ci64 + p * 36 * Vh) : (const void*)(ctx->C64 + p * 36 * Vh);
     Kout = op.kout == 2 ? (const void*)(ctx->C64 + p * 36 * Vh) : (const void*)(ctx->Ci64 + p * 36 * Vh);
   } else if (P == DLMA_FP32) {
-    a.Ua = ctx->U32; a.Ub = nullptr;
+    a.l18 = ctx->hop_l18[P];
+    a.Ua = a.l18 ? (const void*)ctx->U32f : (const void*)ctx->U32;
+    a.Ub = nullptr;
     Kown = op.own == 3 ? (const void*)(ctx->Ci32 + p * 18 * Vh) : (const void*)(ctx->C32 + p * 18 * Vh);
     Kout = op.kout == 2 ? (const void*)(ctx->C32 + p * 18 * Vh) : (const void*)(ctx->Ci32 + p * 18 * Vh);
   } else {
@@ -366,9 +380,10 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   dim3 blk(sx, sy);
   dim3 grid((out.nrhs + sy - 1) / sy, (ctx->g.Vh + sx - 1) / sx);
   if (nblocks_out) *nblocks_out = grid.y;
-  if (P == DLMA_FP64) dispatch<DLMA_FP64>(op, grid, blk, ctx->stream, a);
-  else if (P == DLMA_FP32) dispatch<DLMA_FP32>(op, grid, blk, ctx->stream, a);
-  else dispatch<DLMA_FP16S>(op, grid, blk, ctx->stream, a);
+  if (P == DLMA_FP64) dispatch<DLMA_FP64, false>(op, grid, blk, ctx->stream, a);
+  else if (P == DLMA_FP32 && a.l18) dispatch<DLMA_FP32, true>(op, grid, blk, ctx->stream, a);
+  else if (P == DLMA_FP32) dispatch<DLMA_FP32, false>(op, grid, blk, ctx->stream, a);
+  else dispatch<DLMA_FP16S, false>(op, grid, blk, ctx->stream, a);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
@@ -382,10 +397,18 @@ dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, F
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bx = ctx->hop_sx[prec], by = ctx->hop_sy[prec];
+  int bx = ctx->hop_sx[prec], by = ctx->hop_sy[prec], bl = 0;
+  // FP32: also try 18-real links; DLMA_FORCE_LINKS=12 / 18 pins the format (tests)
+  int l0 = 0, l1 = prec == DLMA_FP32 ? 1 : 0;
+  if (const char* f = getenv("DLMA_FORCE_LINKS")) {
+    if (prec == DLMA_FP32 && atoi(f) == 18) l0 = l1 = 1;
+    if (atoi(f) == 12) l0 = l1 = 0;
+  }
+  for (int l = l0; l <= l1; l++)
   for (const auto& c : cand) {
     ctx->hop_sx[prec] = c[0];
     ctx->hop_sy[prec] = c[1];
+    ctx->hop_l18[prec] = l;
     float tot = 0;
     for (int r = 0; r < 3; r++) {
       CU(cudaEventRecord(e0, ctx->stream));
@@ -396,10 +419,11 @@ dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, F
       CU(cudaEventElapsedTime(&ms, e0, e1));
       if (r > 0) tot += ms;
     }
-    if (tot < best) { best = tot; bx = c[0]; by = c[1]; }
+    if (tot < best) { best = tot; bx = c[0]; by = c[1]; bl = l; }
   }
   ctx->hop_sx[prec] = bx;
   ctx->hop_sy[prec] = by;
+  ctx->hop_l18[prec] = bl;
   ctx->hop_tuned[prec] = 1;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

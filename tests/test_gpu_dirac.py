@@ -64,6 +64,20 @@ def test_apply_dw_low_precision(dl):
         assert _rel(got16[j], want[j]) < 3e-3
 
 
+@pytest.mark.parametrize("links", ["12", "18"])
+def test_schur_fp32_link_formats(dl, links, monkeypatch):
+    # the FP32 stencil reads either 12-real links (third row rebuilt) or all 18 reals
+    monkeypatch.setenv("DLMA_FORCE_LINKS", links)
+    L, T = 6, 4
+    ctx, eo = _ctx(dl, L, T, 0.25, 0.1, 1.2, 111)
+    ve = synth.gaussian_spinors(5, L ** 3 * T // 2, 112)
+    for dagger in (0, 1):
+        got = ctx.dlma_apply_schur(ve, dagger, dl.FP32)
+        want = eo.schur_dag(ve) if dagger else eo.schur(ve)
+        for j in range(5):
+            assert _rel(got[j], want[j]) < 1e-6
+
+
 @pytest.mark.parametrize("dagger", [0, 1])
 def test_schur_fp64(dl, dagger):
     L, T = 6, 4
