@@ -153,6 +153,19 @@ dlma_status dlma_apply_schur_noalloc(dlma_ctx* ctx, const double* in, double* ou
 dlma_status dlma_solve(dlma_ctx* ctx, const double* b, double* x, int nrhs, double tol,
                        dlma_prec inner, dlma_solve_info* info, dlma_mem mem);
 
+/* dlma_solve_adjoint: y = D^-dag g for nrhs full-lattice fields, computed as
+ * gamma_5 D^-1 gamma_5 g (gamma_5-hermiticity; the D^-1^dag of Eq. 3) with the
+ * solver of dlma_solve (same arguments and errors).  The backward pass of a
+ * differentiable solve: for x = D^-1 b, grad_b = D^-dag grad_x and, since
+ * dD/dm0 = 1, dL/dm0 = -Re <D^-dag grad_x, x>. */
+dlma_status dlma_solve_adjoint(dlma_ctx* ctx, const double* g, double* y, int nrhs, double tol,
+                               dlma_prec inner, dlma_solve_info* info, dlma_mem mem);
+
+/* dlma_real_dot: *out = Re sum_i conj(a_i) b_i over n complex numbers (a, b
+ * in `mem`; out HOST).  Errors: INVALID_ARG, CUDA. */
+dlma_status dlma_real_dot(dlma_ctx* ctx, const double* a, const double* b, uint64_t n, double* out,
+                          dlma_mem mem);
+
 /* ---- spatial Laplacian (Eq. 1) --------------------------------------------
  * dlma_apply_laplacian: out = lap(t) in on every timeslice at once for nvec
  * colour fields over the whole lattice (complex [nvec][V][3]):
@@ -218,6 +231,27 @@ dlma_status dlma_contract(dlma_ctx* ctx, int t_src, int N, const double* V, int 
 dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* eta,
                              double tol, dlma_prec inner, double* C_dist, double* C_rest,
                              double* C_mixed, dlma_solve_info* info, dlma_mem mem);
+
+/* dlma_set_checkpoint: on != 0 makes dlma_correlators keep its forward
+ * solutions (the 4N distillation solutions and phi_r, phibar_r of every noise
+ * vector; the Krylov iterates are never kept) for dlma_correlators_backward;
+ * on = 0 releases them. */
+dlma_status dlma_set_checkpoint(dlma_ctx* ctx, int on);
+
+/* dlma_correlators_backward: gradients of L = sum_t w(t) Re C_PS(t), C_PS the
+ * pseudoscalar total C_rest + 2 C_mixed + C_dist of the last checkpointed
+ * dlma_correlators call with the same (t_src, N, n_noise): dL/dm0 (one real,
+ * HOST) and dL/deta (complex [n_noise][L^3][4][3] in `mem`, written as
+ * dL/dRe + i dL/dIm).  w is real [T] in `mem`.  It runs 4N + 2 n_noise adjoint
+ * solves y_j = D^-dag G_j of the adjoint sources G(phi_j) = 2 w Box phi_j
+ * (distillation), G(phi_r) = w/N_r (1 + Box) phibar_r, G(phibar_r) =
+ * w/N_r (1 + Box) phi_r; then dL/dm0 = -sum_j Re <y_j, phi_j> and
+ * dL/deta_r = y_{phi_r} + (1 - Box(t')) y_{phibar_r} on t'.  info (may be NULL)
+ * gets 4N + 2 n_noise records.  Errors: STATE (no checkpoint / modes),
+ * INVALID_ARG, plus those of dlma_solve. */
+dlma_status dlma_correlators_backward(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* w,
+                                      double tol, dlma_prec inner, double* dL_dm0, double* dL_deta,
+                                      dlma_solve_info* info, dlma_mem mem);
 
 /* ---- introspection ---------------------------------------------------------
  * dlma_index_tables: the device's even-odd index arithmetic written out:

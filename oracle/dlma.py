@@ -132,6 +132,48 @@ def dlma_correlators(solve, V_all, eta, L, T, tp):
             "tau": tau, "phi_dist": phid, "phi_noise": phin, "Nc": Nc}
 
 
+def ps_loss(solve, V_all, eta, w, L, T, tp):
+    """L = sum_t w(t) Re C_PS(t) with C_PS = C_rest + 2 C_mixed + C_dist (Eq. 2,
+    Gamma = gamma_5).  Returns (L, correlator dict)."""
+    r = dlma_correlators(solve, V_all, eta, L, T, tp)
+    return float(np.sum(w * r["C"][0].real)), r
+
+
+def ps_loss_grads(solve, solve_dag, V_all, eta, w, L, T, tp):
+    """Adjoint-method gradients of ps_loss with respect to m0 and eta, written
+    as dL/dRe + i dL/dIm.  With Gamma = gamma_5, C_dist = sum |V^dag phi|^2 and
+    C_rest + 2 C_mixed = 1/N_r sum_r <phibar_r, (1 + Box) phi_r>, so
+      G(phi_dist) = 2 w Box phi,  G(phi_r) = w/N_r (1 + Box) phibar_r,
+      G(phibar_r) = w/N_r (1 + Box) phi_r;
+    y = D^-dag G; dL/dm0 = -sum Re <y, phi> (dD/dm0 = 1);
+    dL/deta_r = y_{phi_r} + (1 - Box(t')) y_{phibar_r} on t'."""
+    loss, r = ps_loss(solve, V_all, eta, w, L, T, tp)
+    Nr = eta.shape[0]
+    Vs = L ** 3
+    phid = r["phi_dist"]
+    phi, phibar = r["phi_noise"][:, 0], r["phi_noise"][:, 1]
+
+    def per_t(f, field):
+        out = np.zeros_like(field)
+        for t in range(T):
+            sl = slice(t * Vs, (t + 1) * Vs)
+            out[..., sl, :, :] = f(t, field[..., sl, :, :])
+        return out
+
+    Gd = per_t(lambda t, x: 2 * w[t] * box(V_all[t], x), phid)
+    G_phi = per_t(lambda t, x: w[t] / Nr * (x + box(V_all[t], x)), phibar)
+    G_phibar = per_t(lambda t, x: w[t] / Nr * (x + box(V_all[t], x)), phi)
+    yd = solve_dag(Gd)
+    y_phi = solve_dag(G_phi)
+    y_phibar = solve_dag(G_phibar)
+    dm0 = -(np.vdot(yd.ravel(), phid.ravel()).real + np.vdot(y_phi.ravel(), phi.ravel()).real
+            + np.vdot(y_phibar.ravel(), phibar.ravel()).real)
+    a = timeslice(y_phi, L, tp)
+    b = timeslice(y_phibar, L, tp)
+    deta = a + b - box(V_all[tp], b)
+    return loss, dm0, deta
+
+
 def exact_parts(S, V_all, L, T, tp):
     """Exact (noise-free) correlator pieces from the propagator columns of
     timeslice t'.  S [Vs, 4, 3, V, 4, 3]: S[y, beta, b] = D^-1 (delta_y e_beta e_b).

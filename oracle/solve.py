@@ -48,6 +48,20 @@ def cgne(eo: EvenOdd, b, tol=1e-12, maxiter=20000, check_every=10):
     return xf, it, true_residual(eo, xf, b)
 
 
+def lu_solver_dag(eo: EvenOdd):
+    """Sparse LU of D^dag (the conjugate transpose of the matrix itself, not
+    the gamma_5 identity): maps g [n, V, 4, 3] to D^-dag g."""
+    D = dirac_sparse(eo.U, eo.Tclov, eo.L, eo.T, eo.bc_t).conj().T.tocsc()
+    lu = spla.splu(D)
+    V = eo.V
+
+    def solve(g):
+        x = lu.solve(np.ascontiguousarray(g.reshape(-1, 12 * V).T))
+        return x.T.reshape(g.shape)
+
+    return solve
+
+
 def lu_solver(eo: EvenOdd):
     """Sparse LU factorisation of the full D (library routine; the dense-LU
     cross-check).  Returns a function mapping sources [n, V, 4, 3] to

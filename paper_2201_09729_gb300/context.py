@@ -134,6 +134,41 @@ class Context:
         return x, [dict(iters_inner=i.iters_inner, iters_outer=i.iters_outer, true_resid=i.true_resid,
                         converged=bool(i.converged)) for i in info]
 
+    def dlma_solve_adjoint(self, g, tol: float, inner: int = L.FP64):
+        n = g.shape[0]
+        _check_c128(g, (n, self.V, 4, 3), "g")
+        y = _empty_like(g, g.shape)
+        info = (L.SolveInfo * n)()
+        self._check(self.lib.dlma_solve_adjoint(self.h, _ptr(g), _ptr(y), n, float(tol), inner, info, _mem(g)))
+        return y
+
+    def dlma_real_dot(self, a, b) -> float:
+        if tuple(a.shape) != tuple(b.shape):
+            raise ValueError("shape mismatch")
+        n = 1
+        for s in a.shape:
+            n *= int(s)
+        out = C.c_double()
+        self._check(self.lib.dlma_real_dot(self.h, _ptr(a), _ptr(b), n, C.byref(out), _mem(a)))
+        return out.value
+
+    def dlma_set_checkpoint(self, on: bool):
+        self._check(self.lib.dlma_set_checkpoint(self.h, 1 if on else 0))
+
+    def dlma_correlators_backward(self, t_src: int, N: int, n_noise: int, w, tol: float, inner: int = L.FP32):
+        """(dL/dm0, dL/deta) of L = sum_t w(t) Re C_PS(t) for the last checkpointed forward."""
+        if _is_torch(w):
+            import torch
+            w = w.detach().to(torch.float64).contiguous()
+            deta = torch.empty((n_noise, self.Vs, 4, 3), dtype=torch.complex128, device=w.device)
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            deta = np.empty((n_noise, self.Vs, 4, 3), dtype=np.complex128)
+        dm0 = C.c_double()
+        self._check(self.lib.dlma_correlators_backward(self.h, int(t_src), int(N), int(n_noise), _ptr(w),
+                                                       float(tol), inner, C.byref(dm0), _ptr(deta), None, _mem(w)))
+        return dm0.value, deta
+
     def dlma_apply_laplacian(self, v):
         n = v.shape[0]
         _check_c128(v, (n, self.V, 3), "v")

@@ -128,6 +128,12 @@ struct dlma_ctx {
   std::vector<double> eig_lam;    // [T][N]
   std::vector<int> eig_have;      // [T] modes cached for timeslice t
 
+  // checkpointed forward solutions of dlma_correlators (for the backward):
+  // [4N distillation, then phi_r, phibar_r per noise][V][4][3] complex
+  int checkpoint = 0;
+  double* ckpt = nullptr;
+  int ckpt_J = 0, ckpt_N = 0, ckpt_nn = 0, ckpt_tsrc = -1;
+
   // named work buffers
   DevBuf wb[64];
   void* pinned = nullptr;         // small pinned host staging area

@@ -314,6 +314,16 @@ static dlma_status project(dlma_ctx* ctx, const double2* VT, int N, int Tsel, co
   return DLMA_OK;
 }
 
+// the same helpers for the backward pass (grad.cu)
+dlma_status contract_transpose_V(dlma_ctx* ctx, const double* V, int st_t, int st_k, int Tsel, int t0, int N,
+                                 double2** VT, int slot) {
+  return transpose_V(ctx, V, st_t, st_k, Tsel, t0, N, VT, slot);
+}
+dlma_status contract_project(dlma_ctx* ctx, const double2* VT, int N, int Tsel, const double* psi,
+                             size_t stride_sites, int site_t0, int nrhs, double2* coeff) {
+  return project(ctx, VT, N, Tsel, psi, stride_sites, site_t0, nrhs, coeff);
+}
+
 // (1 - Box(t')) eta for all noise vectors: pe [nn][Vs][4][3]
 static dlma_status project_noise(dlma_ctx* ctx, const double2* VTs, int N, const double* eta, int nn, double2** pe) {
   const int Vs = ctx->g.Vs;
@@ -507,6 +517,24 @@ extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_n
   double *b, *x;
   TRY(workT(ctx, WS_SRC, (size_t)nb * V * 24, &b));
   TRY(workT(ctx, WS_SOL, (size_t)nb * V * 24, &x));
+  // checkpoint (for dlma_correlators_backward): distillation solutions and phi_r, phibar_r
+  const int J2 = 4 * N + 2 * n_noise;
+  const size_t fbytes = V * 12 * 16;
+  if (ctx->checkpoint) {
+    if (ctx->ckpt_J < J2) {
+      if (ctx->ckpt) cudaFree(ctx->ckpt);
+      ctx->ckpt = nullptr;
+      ctx->ckpt_J = 0;
+      if (cudaMalloc(&ctx->ckpt, (size_t)J2 * fbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, DLMA_ERR_OOM, "checkpoint of %d solutions does not fit", J2);
+      }
+      ctx->ckpt_J = J2;
+    }
+    ctx->ckpt_N = N;
+    ctx->ckpt_nn = n_noise;
+    ctx->ckpt_tsrc = t_src;
+  }
   dlma_status worst = DLMA_OK;
   // distillation rows in chunks of nb, then noise rows in whole groups of 5
   int j0 = 0;
@@ -522,6 +550,17 @@ extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_n
     if (j0 >= 4 * N) {
       int r0 = (j0 - 4 * N) / 5;
       TRY(spin_inner(ctx, x, cnt / 5, 0, M + (size_t)r0 * 4 * T * 16));
+    }
+    if (ctx->checkpoint) {
+      if (j0 < 4 * N) {
+        CU(cudaMemcpyAsync(ctx->ckpt + (size_t)j0 * V * 24, x, (size_t)cnt * fbytes, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+      } else {
+        const int r0 = (j0 - 4 * N) / 5;
+        for (int r = 0; r < cnt / 5; r++)
+          CU(cudaMemcpyAsync(ctx->ckpt + ((size_t)4 * N + 2 * (r0 + r)) * V * 24, x + (size_t)5 * r * V * 24,
+                             2 * fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
     }
     j0 += cnt;
   }

@@ -390,6 +390,7 @@ static void free_all(dlma_ctx* ctx) {
                   ctx->C32, ctx->Ci32, ctx->C16, ctx->Ci16, ctx->flag, ctx->eig_V};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (ctx->ckpt) cudaFree(ctx->ckpt);
   for (int i = 0; i < WS_COUNT; i++)
     if (ctx->wb[i].p) cudaFree(ctx->wb[i].p);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);

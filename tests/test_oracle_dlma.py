@@ -95,3 +95,29 @@ def test_planted_mistake_is_caught(small):
     gap_ok = np.abs(m_ok[0] - ex["mixed_snk"][0]).max()
     gap_bad = np.abs(m_bad[0] - ex["mixed_snk"][0]).max()
     assert gap_bad > 3 * gap_ok
+
+
+def test_ps_loss_adjoint_matches_finite_differences():
+    # the oracle's adjoint gradients of L = sum_t w(t) Re C_PS(t) against central
+    # differences of L itself (in m0 and along a random complex direction of eta)
+    L_, T, N, nn, csw, m0 = 4, 4, 3, 2, 1.0, 0.12
+    U = synth.gauge_field(L_, T, 0.2, 48)
+    V_all = np.stack([lap.lap_modes(lap.timeslice_links(U, L_, t), L_, N)[1] for t in range(T)])
+    eta = synth.z2z2_noise(nn, L_ ** 3, 49)
+    w = synth.loss_weights(T, 50)
+
+    def solvers(m):
+        eo = dirac.EvenOdd(U, L_, T, m, csw)
+        return solve.lu_solver(eo), solve.lu_solver_dag(eo)
+
+    s, sd = solvers(m0)
+    loss, dm0, deta = dlma.ps_loss_grads(s, sd, V_all, eta, w, L_, T, 0)
+    h = 1e-4
+    lp = dlma.ps_loss(solvers(m0 + h)[0], V_all, eta, w, L_, T, 0)[0]
+    lm = dlma.ps_loss(solvers(m0 - h)[0], V_all, eta, w, L_, T, 0)[0]
+    assert abs((lp - lm) / (2 * h) - dm0) < 1e-6 * abs(dm0)
+    d = synth.gaussian_spinors(nn, L_ ** 3, 51)
+    lp = dlma.ps_loss(s, V_all, eta + h * d, w, L_, T, 0)[0]
+    lm = dlma.ps_loss(s, V_all, eta - h * d, w, L_, T, 0)[0]
+    want = np.vdot(deta.ravel(), d.ravel()).real
+    assert abs((lp - lm) / (2 * h) - want) < 1e-6 * abs(want)
