@@ -83,6 +83,10 @@ typedef struct {
 dlma_status dlma_create(const dlma_lattice* lat, int device, void* cuda_stream, dlma_ctx** out);
 dlma_status dlma_destroy(dlma_ctx* ctx);
 const char* dlma_last_error(const dlma_ctx* ctx);
+/* Free the context's work space (solver, eigensolver and contraction buffers
+ * grow on demand and are kept between calls); the gauge and clover fields, the
+ * cached modes and any checkpoint stay.  Errors: INVALID_ARG. */
+dlma_status dlma_release_workspace(dlma_ctx* ctx);
 /* Cap on the library's own device work space in bytes (0 = no cap); solves
  * that would exceed it run in smaller batches, or fail with OOM if one
  * right-hand side does not fit. */

@@ -39,6 +39,7 @@ SIGNATURES = {
     "dlma_destroy": (_ST, [_P]),
     "dlma_last_error": (C.c_char_p, [_P]),
     "dlma_set_memory_cap": (_ST, [_P, C.c_uint64]),
+    "dlma_release_workspace": (_ST, [_P]),
     "dlma_set_gauge": (_ST, [_P, _P, _I]),
     "dlma_set_params": (_ST, [_P, _D, _D]),
     "dlma_apply_Dw": (_ST, [_P, _P, _P, _I, _I, _I]),

@@ -103,6 +103,9 @@ class Context:
     def dlma_set_memory_cap(self, nbytes: int):
         self._check(self.lib.dlma_set_memory_cap(self.h, int(nbytes)))
 
+    def dlma_release_workspace(self):
+        self._check(self.lib.dlma_release_workspace(self.h))
+
     def dlma_set_gauge(self, U):
         _check_c128(U, (self.V, 4, 3, 3), "links")
         self._check(self.lib.dlma_set_gauge(self.h, _ptr(U), _mem(U)))

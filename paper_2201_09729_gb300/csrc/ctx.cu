@@ -474,6 +474,19 @@ extern "C" dlma_status dlma_destroy(dlma_ctx* ctx) {
 
 extern "C" const char* dlma_last_error(const dlma_ctx* ctx) { return ctx ? ctx->err : "null context"; }
 
+extern "C" dlma_status dlma_release_workspace(dlma_ctx* ctx) {
+  if (!ctx) return DLMA_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (int i = 0; i < WS_COUNT; i++) {
+    if (ctx->wb[i].p) cudaFree(ctx->wb[i].p);
+    ctx->wb[i].p = nullptr;
+    ctx->wb[i].bytes = 0;
+  }
+  ctx->work_bytes = 0;
+  return DLMA_OK;
+}
+
 extern "C" dlma_status dlma_set_memory_cap(dlma_ctx* ctx, uint64_t bytes) {
   if (!ctx) return DLMA_ERR_INVALID_ARG;
   ctx->memcap = bytes;
