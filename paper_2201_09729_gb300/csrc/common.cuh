@@ -229,6 +229,12 @@ struct HopOp {
   double s = 1.0;     // sign / factor of the hopping term
   double* norm_part = nullptr;   // if set: per (rhs, block) partial |out|^2
   const int* active = nullptr;   // per-rhs mask (nullptr = all)
+  // fused CG update instead of storing the output (Schur step B of the adjoint):
+  // x += alpha p, r -= alpha out, partial |r|^2 into norm_part
+  void* cg_x = nullptr;
+  void* cg_r = nullptr;
+  const void* cg_p = nullptr;
+  const double* cg_alpha = nullptr;
 };
 dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Field* own, Field& out,
                        int* nblocks_out = nullptr);
@@ -238,6 +244,10 @@ int hop_grid_x(dlma_ctx* ctx, int prec);
 dlma_status schur_apply(dlma_ctx* ctx, const Field& in, Field& tmp, Field& out, int dagger,
                         const int* active, double* norm_part);
 dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, Field& out);
+// z = Dhat^dag q fused with the CG update x += alpha p, r -= alpha z (x, r, p in the
+// vector precision); partial |r|^2 per (rhs, site tile) into part
+dlma_status schur_dag_cgupdate(dlma_ctx* ctx, const Field& q, Field& tmp, const int* active, Field& x, Field& r,
+                               const Field& p, const double* alpha, double* part);
 
 void gamma_matrices(double G[4][4][4][2]);
 dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol,

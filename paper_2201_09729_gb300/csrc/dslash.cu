@@ -145,6 +145,9 @@ struct HopArgs {
   const int* active;
   const int4* nbr;    // neighbour table (dlma_ctx::nbr_tab)
   int l18;            // FP32: Ua holds 18-real links
+  // CG epilogue (CGU): with z the result at this site, x += alpha p, r -= alpha z
+  // (vector precision PB = FP64 for an FP64 stencil, FP32 otherwise), partial |r|^2
+  void* cg_x; void* cg_r; const void* cg_p; const double* cg_alpha; size_t cg_stride;
 };
 
 template <class R>
@@ -169,7 +172,7 @@ __device__ __forceinline__ void su3_dag_mul(const Cx<R> U[3][3], const Cx<R> h[3
   }
 }
 
-template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM, bool L18>
+template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM, bool L18, bool CGU = false>
 __global__ void __launch_bounds__(256, P == DLMA_FP64 ? 2 : 3) k_hop(HopArgs a) {
   typedef typename PT<P>::R R;
   // grid x runs over right-hand-side groups (fast), grid y over site tiles: all
@@ -266,9 +269,30 @@ __global__ void __launch_bounds__(256, P == DLMA_FP64 ? 2 : 3) k_hop(HopArgs a) 
         for (int c = 0; c < 3; c++) res.c[s][c] = res.c[s][c] + o.c[s][c];
     }
     if (KOUT) clover_apply<P>(a.Kout, i, g.Vh, res);
-    store_spinor<P>((char*)a.out + (size_t)j * a.out_stride, a.out_scale ? a.out_scale + (size_t)j * g.Vh : nullptr,
-                    g.Vh, i, res);
-    if (NORM) {
+    if (CGU) {
+      // fused CG update: z (= res) is consumed here and never stored
+      constexpr int PB = P == DLMA_FP64 ? DLMA_FP64 : DLMA_FP32;
+      typedef typename PT<PB>::R RB;
+      const size_t sb = (size_t)j * a.cg_stride;
+      const RB al = (RB)a.cg_alpha[j];
+      Spinor<RB> xv = load_spinor<PB>((char*)a.cg_x + sb, nullptr, g.Vh, i);
+      Spinor<RB> rv = load_spinor<PB>((char*)a.cg_r + sb, nullptr, g.Vh, i);
+      const Spinor<RB> pv = load_spinor<PB>((const char*)a.cg_p + sb, nullptr, g.Vh, i);
+#pragma unroll
+      for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          xv.c[s][c] = xv.c[s][c] + al * pv.c[s][c];
+          rv.c[s][c] = rv.c[s][c] - al * cx<RB>((RB)res.c[s][c].re, (RB)res.c[s][c].im);
+          nrm += (double)norm2(rv.c[s][c]);
+        }
+      store_spinor<PB>((char*)a.cg_x + sb, nullptr, g.Vh, i, xv);
+      store_spinor<PB>((char*)a.cg_r + sb, nullptr, g.Vh, i, rv);
+    } else {
+      store_spinor<P>((char*)a.out + (size_t)j * a.out_stride, a.out_scale ? a.out_scale + (size_t)j * g.Vh : nullptr,
+                      g.Vh, i, res);
+    }
+    if (NORM && !CGU) {
 #pragma unroll
       for (int s = 0; s < 4; s++)
 #pragma unroll
@@ -316,6 +340,10 @@ static void dispatch(const HopOp& op, dim3 grid, dim3 blk, cudaStream_t st, cons
     else L(false, false, 1, false, false, false);
     return;
   }
+  if (op.cg_x) {                                   // Schur step B of the adjoint + CG update
+    k_hop<P, false, true, 2, false, true, true, L18, true><<<grid, blk, 0, st>>>(a);
+    return;
+  }
   if (op.own == 0 && op.kout) {                    // Schur step A (and its dagger)
     if (op.g5_in) L(true, false, 0, true, true, false);
     else L(false, false, 0, true, true, false);
@@ -354,6 +382,11 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   a.active = op.active;
   a.nbr = ctx->nbr_tab;
   a.l18 = 0;
+  a.cg_x = op.cg_x;
+  a.cg_r = op.cg_r;
+  a.cg_p = op.cg_p;
+  a.cg_alpha = op.cg_alpha;
+  a.cg_stride = field_units_per_rhs(P == DLMA_FP64 ? DLMA_FP64 : DLMA_FP32, ctx->g.Vh) * 16;
   const size_t Vh = ctx->g.Vh;
   const int p = op.p_out;
   const void* Kown = nullptr;
@@ -427,6 +460,32 @@ dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, F
   ctx->hop_tuned[prec] = 1;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  return DLMA_OK;
+}
+
+dlma_status schur_dag_cgupdate(dlma_ctx* ctx, const Field& q, Field& tmp, const int* active, Field& x, Field& r,
+                               const Field& p, const double* alpha, double* part) {
+  HopOp A;
+  A.p_out = 1;
+  A.own = 0;
+  A.kout = 3;
+  A.g5_in = 1;
+  A.active = active;
+  TRY(launch_hop(ctx, A, q, nullptr, tmp));
+  HopOp B;
+  B.p_out = 0;
+  B.own = 2;
+  B.kout = 0;
+  B.g5_hop = 1;
+  B.s = -1.0;
+  B.active = active;
+  B.norm_part = part;
+  B.cg_x = x.data;
+  B.cg_r = r.data;
+  B.cg_p = p.data;
+  B.cg_alpha = alpha;
+  Field dummy = q;      // output not stored: the CG epilogue consumes it
+  TRY(launch_hop(ctx, B, tmp, &q, dummy));
   return DLMA_OK;
 }
 

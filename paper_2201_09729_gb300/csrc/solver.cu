@@ -343,12 +343,9 @@ static dlma_status inner_iteration(dlma_ctx* ctx, SolveBufs& B, int nrhs, int ma
   TRY(schur_apply(ctx, B.ps, B.tmp, B.q, 0, B.sc.active, B.part));
   k_cg_alpha<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(B.part, nbh, nrhs, B.sc);
   CHECK_LAUNCH();
-  // z = Dhat^dag q
-  TRY(schur_apply(ctx, B.q, B.tmp, B.z, 1, B.sc.active, nullptr));
-  k_update_xr<PB, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.xl.data, B.rl.data, B.pl.data, B.z.data, B.z.scale,
-                                                  B.sc, B.part2);
-  CHECK_LAUNCH();
-  k_cg_beta<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(B.part2, gv.x, nrhs, B.sc, max_since, delta2);
+  // z = Dhat^dag q with the update x += alpha p, r -= alpha z fused into its epilogue
+  TRY(schur_dag_cgupdate(ctx, B.q, B.tmp, B.sc.active, B.xl, B.rl, B.pl, B.sc.alpha, B.part2));
+  k_cg_beta<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(B.part2, nbh, nrhs, B.sc, max_since, delta2);
   CHECK_LAUNCH();
   k_update_p<PB, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, B.pl.data, B.ps.data, B.ps.scale, B.sc);
   CHECK_LAUNCH();
