@@ -139,37 +139,6 @@ template <class R> __device__ __forceinline__ double snorm(const Spinor<R>& s) {
   return n;
 }
 
-// x += alpha p; r -= alpha z; partial |r|^2           (PB: vector precision, PS: stencil precision)
-template <int PB, int PS>
-__global__ void __launch_bounds__(BX) k_update_xr(int Vh, int nrhs, void* x, void* r, const void* p, const void* z,
-                                                   const float* zsc, CgScal sc, double* part) {
-  typedef typename PT<PB>::R R;
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y;
-  const bool on = sc.active[j] != 0;
-  double n = 0;
-  if (i < Vh && on) {
-    const size_t sb = field_units_per_rhs(PB, Vh) * 16 * j, ss = field_units_per_rhs(PS, Vh) * 16 * j;
-    const R a = (R)sc.alpha[j];
-    Spinor<R> xv = load_spinor<PB>((char*)x + sb, nullptr, Vh, i);
-    Spinor<R> rv = load_spinor<PB>((char*)r + sb, nullptr, Vh, i);
-    const Spinor<R> pv = load_spinor<PB>((const char*)p + sb, nullptr, Vh, i);
-    const Spinor<typename PT<PS>::R> zv =
-        load_spinor<PS>((const char*)z + ss, zsc ? zsc + (size_t)j * Vh : nullptr, Vh, i);
-#pragma unroll
-    for (int s = 0; s < 4; s++)
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        xv.c[s][c] = xv.c[s][c] + a * pv.c[s][c];
-        rv.c[s][c] = rv.c[s][c] - a * cx<R>((R)zv.c[s][c].re, (R)zv.c[s][c].im);
-      }
-    store_spinor<PB>((char*)x + sb, nullptr, Vh, i, xv);
-    store_spinor<PB>((char*)r + sb, nullptr, Vh, i, rv);
-    n = snorm(rv);
-  }
-  block_partial(n, part, on ? j : nrhs, nrhs);
-}
-
 // p = r + beta p  (and the stencil-precision copy when PS != PB)
 template <int PB, int PS>
 __global__ void __launch_bounds__(BX) k_update_p(int Vh, int nrhs, const void* r, void* p, void* ps, float* pssc,

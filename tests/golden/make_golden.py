@@ -32,7 +32,7 @@ def main():
     dt = time.time() - t0
     out = {
         "workload": wl.name,
-        "source": "Z2xZ2 noise on t'=0 (noise seed 20222126, first vector)",
+        "source": f"Z2xZ2 noise on t'=0 (noise seed {synth.NOISE_SEED_BASE + wl.cfg}, first vector)",
         "tol": wl.tol,
         "iterations": int(iters),
         "true_residual": float(res),
