@@ -70,8 +70,11 @@ typedef struct {
 
 typedef struct {
   int iters_inner;     /* inner (low-precision) Krylov iterations summed over restarts */
-  int iters_outer;     /* FP64 defect-correction restarts */
-  double true_resid;   /* ||b - D x||_2 / ||b||_2 on the full lattice, recomputed in FP64 */
+  int iters_outer;     /* FP64 reliable updates (residual replacements) */
+  double true_resid;   /* ||b - D x||_2 / ||b||_2 in FP64: the even-odd Schur residual
+                          |bhat - Dhat x_e| of the final FP64 update (the odd rows of
+                          b - D x vanish by construction of x_o), or, for a solve stopped
+                          before converging, b - D x evaluated on the full lattice */
   int converged;       /* 1 if true_resid <= tol */
 } dlma_solve_info;
 

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(256, P == DLMA_FP64 ? 2 : 3) k_hop(HopArgs a) 
 #pragma unroll
         for (int dir = 0; dir < 2; dir++) {
           const int raw = nb8[2 * mu + dir];
-          const int n = raw & 0x7fffffff;
+          const int n = mu == 0 ? (raw & 0x7fffffff) : raw;   // only time neighbours carry the phase bit
           Spinor<R> ps = load_spinor<P>(in_j, sc_j, g.Vh, n);
           if (G5IN) {
 #pragma unroll
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256, P == DLMA_FP64 ? 2 : 3) k_hop(HopArgs a) 
           Cx<R> U[3][3];
           // forward: U_mu(x) at this site; backward: U_mu(x - mu) at the neighbour
           load_link<P>(a.Ua, a.Ub, dir == 0 ? a.p_out : 1 - a.p_out, mu, dir == 0 ? i : n, g.Vh, U, L18);
-          const R ph = raw < 0 ? (R)-1 : (R)1;    // antiperiodic time phase (bit 31)
+          const R ph = raw < 0 ? (R)-1 : (R)1;    // antiperiodic time phase (bit 31, mu = 0 only)
           Cx<R> h0[3], h1[3], w0[3], w1[3];
 #pragma unroll
           for (int c = 0; c < 3; c++) {
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256, P == DLMA_FP64 ? 2 : 3) k_hop(HopArgs a) 
           else { su3_dag_mul(U, h0, w0); su3_dag_mul(U, h1, w1); }
 #pragma unroll
           for (int c = 0; c < 3; c++) {
-            const Cx<R> x0 = ph * w0[c], x1 = ph * w1[c];
+            const Cx<R> x0 = mu == 0 ? ph * w0[c] : w0[c], x1 = mu == 0 ? ph * w1[c] : w1[c];
             res.c[0][c] = res.c[0][c] + x0;
             res.c[1][c] = res.c[1][c] + x1;
             if (dir == 0) {

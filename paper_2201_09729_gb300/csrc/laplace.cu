@@ -125,14 +125,23 @@ __global__ void __launch_bounds__(256) k_lap(Geom g, int t0, int Tn, int m, cons
 }
 
 // Gram partials: part[t][split][i][j] = sum_{k in chunk} conj(X_t[k][i]) Y_t[k][j]
+// herm: the product is hermitian (X^dag X, or Y^dag A Y with A hermitian): only the
+// tiles on and above the diagonal are computed, k_gram_reduce mirrors the rest
 constexpr int GT = 32, GKS = 32;
 template <class R>
 __global__ void __launch_bounds__(256) k_gram(const Cx<R>* __restrict__ X, const Cx<R>* __restrict__ Y, int n, int m,
-                                              int nsplit, double2* part) {
+                                              int nsplit, int herm, double2* part) {
   __shared__ Cx<R> xs[GKS][GT + 1];
   __shared__ Cx<R> ys[GKS][GT + 1];
   const int tiles_j = (m + GT - 1) / GT;
-  const int i0 = (blockIdx.x / tiles_j) * GT, j0 = (blockIdx.x % tiles_j) * GT;
+  int ti = blockIdx.x / tiles_j, tj = blockIdx.x % tiles_j;
+  if (herm) {                 // blockIdx.x enumerates the pairs ti <= tj row by row
+    int b = blockIdx.x;
+    ti = 0;
+    while (b >= tiles_j - ti) { b -= tiles_j - ti; ti++; }
+    tj = ti + b;
+  }
+  const int i0 = ti * GT, j0 = tj * GT;
   const int split = blockIdx.y, t = blockIdx.z;
   const int chunk = (n + nsplit - 1) / nsplit;
   const int k0 = split * chunk, k1 = min(n, k0 + chunk);
@@ -179,17 +188,21 @@ __global__ void __launch_bounds__(256) k_gram(const Cx<R>* __restrict__ X, const
     }
 }
 
-__global__ void k_gram_reduce(const double2* part, int nsplit, int m, int Tn, double2* G) {
+__global__ void k_gram_reduce(const double2* part, int nsplit, int m, int Tn, int herm, double2* G) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t per = (size_t)m * m;
   if (e >= per * Tn) return;
-  const size_t t = e / per, ij = e % per;
+  const size_t t = e / per;
+  const int i = (int)((e % per) / m), j = (int)(e % m);
+  const bool mirror = herm && (i / GT) > (j / GT);    // tile below the diagonal: conj of (j, i)
+  const size_t ij = mirror ? (size_t)j * m + i : (size_t)i * m + j;
   double2 s = make_double2(0, 0);
   for (int q = 0; q < nsplit; q++) {
     const double2 v = part[(t * nsplit + q) * per + ij];
     s.x += v.x;
     s.y += v.y;
   }
+  if (mirror) s.y = -s.y;
   G[e] = s;
 }
 
@@ -378,7 +391,8 @@ struct Eig {
   Cx<double> *D0, *D1, *D2;      // FP64 blocks
   double2 *G, *H, *C, *part, *gwork;
   double *theta, *res, *coef, *scol;
-  int* dropped;
+  int* dropped;                  // [0] dropped directions of the last small_rr, [1 + 2t + {0,1}] Jacobi sweeps
+  bool refilled = false;         // the last fetch refilled dropped columns
   double drop_rel;
   uint64_t refill_seed;
   std::vector<double> th, rs;
@@ -399,13 +413,15 @@ static dlma_status lap(Eig& E, const Cx<R>* in, const Cx<R>* prev, const Cx<floa
   return DLMA_OK;
 }
 
-template <class R> static dlma_status gram(Eig& E, const Cx<R>* X, const Cx<R>* Y, double2* out) {
+// out = X^dag Y per timeslice; herm = 1 when the result is hermitian by construction
+template <class R> static dlma_status gram(Eig& E, const Cx<R>* X, const Cx<R>* Y, double2* out, int herm) {
   dlma_ctx* ctx = E.ctx;
-  const int tiles = ((E.m + GT - 1) / GT) * ((E.m + GT - 1) / GT);
-  k_gram<R><<<dim3(tiles, E.nsplit, E.Tn), 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, E.part);
+  const int tj = (E.m + GT - 1) / GT;
+  const int tiles = herm ? tj * (tj + 1) / 2 : tj * tj;
+  k_gram<R><<<dim3(tiles, E.nsplit, E.Tn), 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, herm, E.part);
   CHECK_LAUNCH();
   const size_t tot = (size_t)E.m * E.m * E.Tn;
-  k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(E.part, E.nsplit, E.m, E.Tn, out);
+  k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(E.part, E.nsplit, E.m, E.Tn, herm, out);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
@@ -428,6 +444,18 @@ template <class T> static dlma_status small_rr(Eig& E) {
   k_small_rr<T><<<E.Tn, 256, use_smem ? sm : 0, ctx->stream>>>(E.G, E.H, E.m, E.C, E.theta, (Cx<T>*)E.gwork,
                                                                use_smem, E.dropped, E.drop_rel);
   CHECK_LAUNCH();
+  if (getenv("DLMA_DEBUG_EIG")) {   // Jacobi sweeps of the two eigenproblems, per timeslice
+    std::vector<int> sw(2 * E.Tn);
+    CU(cudaMemcpyAsync(sw.data(), E.dropped + 1, sizeof(int) * 2 * E.Tn, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    int g0 = 1 << 30, g1 = 0, h0 = 1 << 30, h1 = 0;
+    for (int t = 0; t < E.Tn; t++) {
+      g0 = std::min(g0, sw[2 * t]); g1 = std::max(g1, sw[2 * t]);
+      h0 = std::min(h0, sw[2 * t + 1]); h1 = std::max(h1, sw[2 * t + 1]);
+    }
+    fprintf(stderr, "[eig] small_rr<%s> m=%d: Gram sweeps %d..%d, H sweeps %d..%d\n",
+            sizeof(T) == 4 ? "float" : "double", E.m, g0, g1, h0, h1);
+  }
   return DLMA_OK;
 }
 
@@ -436,8 +464,8 @@ template <class R>
 static dlma_status rayleigh_ritz(Eig& E, Cx<R>* Y, Cx<R>* W, Cx<R>* Xout, Cx<R>* AXout, Cx<float>* Rout,
                                  const double* coef_plain) {
   TRY(lap<R>(E, Y, nullptr, nullptr, nullptr, W, coef_plain));
-  TRY(gram<R>(E, Y, Y, E.G));
-  TRY(gram<R>(E, Y, W, E.H));
+  TRY(gram<R>(E, Y, Y, E.G, 1));
+  TRY(gram<R>(E, Y, W, E.H, 1));
   TRY(small_rr<R>(E));
   TRY(rotate<R>(E, Y, Xout));
   TRY(rotate<R>(E, W, AXout));
@@ -459,6 +487,7 @@ template <class R> static dlma_status fetch(Eig& E, double* worst, Cx<R>* X) {
   int hdrop = 0;
   CU(cudaMemcpyAsync(&hdrop, E.dropped, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
+  E.refilled = hdrop != 0;
   if (hdrop) {
     k_refill<R><<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X, E.theta, E.n, E.m, E.blk,
                                                                          E.refill_seed++);
@@ -581,7 +610,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   const int d = E.degree;
   double* aux;
   const size_t ncoef = (size_t)(d + 1) * 3 * Tn, nscol = (size_t)(d + 1) * Tn * m;
-  TRY(workT(ctx, WS_EIG_AUX, 2 * (size_t)m * Tn + ncoef + nscol + 16, &aux));
+  TRY(workT(ctx, WS_EIG_AUX, 2 * (size_t)m * Tn + ncoef + nscol + Tn + 16, &aux));
   E.theta = aux;
   E.res = aux + (size_t)m * Tn;
   E.coef = E.res + (size_t)m * Tn;
@@ -639,7 +668,10 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   Cx<float>* X = p3[0];
   // ---- phase B: FP64 Ritz vectors, FP32 residual-driven filter ----
   Cx<double> *X64 = E.D0, *W64 = E.D1, *Y64 = E.D2;
-  k_convert_block<float, double><<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X, Y64, E.blk);
+  // phase A's last Ritz pairs were not fetched, or hold refilled (random) columns
+  const bool rr_first = E.refilled || it >= maxA;
+  k_convert_block<float, double><<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X, rr_first ? Y64 : X64,
+                                                                                           E.blk);
   CHECK_LAUNCH();
   Cx<float>* R32 = E.F3;   // residual R = AX - X Theta
   Cx<float>* Ebuf[3];
@@ -649,9 +681,17 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
     for (int i = 0; i < 4; i++)
       if (all[i] != R32) Ebuf[q++] = all[i];
   }
-  // Rayleigh-Ritz in FP64 on the FP32 result: X64 = Ritz vectors, Y64 = A X64, R32 = AX - X Theta
+  // The filter below needs only R32 = A X - X Theta for the current X and Theta, which
+  // hold for phase A's Ritz pairs as they stand: X64 = X, Y64 = A X64, R32.  After a
+  // refill the block is first re-diagonalised in FP64.
   E.drop_rel = 1e-24;
-  TRY(rayleigh_ritz<double>(E, Y64, W64, X64, Y64, R32, plain));
+  if (rr_first) {
+    TRY(rayleigh_ritz<double>(E, Y64, W64, X64, Y64, R32, plain));
+  } else {
+    TRY(lap<double>(E, X64, nullptr, nullptr, nullptr, Y64, plain));
+    k_resid<double><<<dim3((m + 31) / 32, Tn), 256, 0, ctx->stream>>>(X64, Y64, E.theta, E.n, m, E.res, R32);
+    CHECK_LAUNCH();
+  }
   bool conv = false;
   int itB = 0;
   int dB = d;
@@ -678,11 +718,11 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
     CHECK_LAUNCH();
     // Rayleigh-Ritz of Y64: W64 = A Y64; X64 <- Y64 C; AX into W... (use X64 as output: Y64 and W64 are inputs)
     TRY(lap<double>(E, Y64, nullptr, nullptr, nullptr, W64, plain));
-    TRY(gram<double>(E, Y64, Y64, E.G));
-    TRY(gram<double>(E, Y64, W64, E.H));
+    TRY(gram<double>(E, Y64, Y64, E.G, 1));
+    TRY(gram<double>(E, Y64, W64, E.H, 1));
     TRY(small_rr<double>(E));
     TRY(rotate<double>(E, Y64, X64));
-    TRY(rotate<double>(E, W64, Y64));   // A X (Y64 is free after the rotation above)
+    TRY(lap<double>(E, X64, nullptr, nullptr, nullptr, Y64, plain));   // A X, fresh (cheaper than W C)
     k_resid<double><<<dim3((m + 31) / 32, Tn), 256, 0, ctx->stream>>>(X64, Y64, E.theta, E.n, m, E.res, R32);
     CHECK_LAUNCH();
   }

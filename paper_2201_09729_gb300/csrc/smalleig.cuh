@@ -22,9 +22,10 @@ template <> struct SmallPrec<double> { static constexpr double eps = 1e-15; };
 __device__ __forceinline__ int rr_pos(int idx, int r, int m) { return idx == 0 ? 0 : ((idx - 1 + r) % (m - 1)) + 1; }
 
 // Diagonalise the hermitian A [m][m] (row-major, in place), accumulating the
-// rotations into the columns of V (which holds the initial basis).
+// rotations into the columns of V (which holds the initial basis).  Returns the
+// number of sweeps.
 template <class T>
-__device__ void jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, double* red) {
+__device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, double* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int np = m / 2;
   __shared__ int rotated;
@@ -37,7 +38,8 @@ __device__ void jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, doubl
   __syncthreads();
   // entries below this absolute floor are rounding noise even next to tiny diagonals
   const T floor_abs = (T)(1e-4 * (double)SmallPrec<T>::eps * dmax);
-  for (int sweep = 0; sweep < 40; sweep++) {
+  int sweep = 0;
+  for (; sweep < 40; sweep++) {
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int r = 0; r < m - 1; r++) {
@@ -89,6 +91,7 @@ __device__ void jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, doubl
     __syncthreads();
   }
   (void)red;
+  return sweep + 1;
 }
 
 template <class T>
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(256) k_small_rr(const double2* Gall, const dou
     S[e] = cx<T>((e / m) == (e % m) ? (T)1 : (T)0, 0);
   }
   __syncthreads();
-  jacobi<T>(A, S, m, rc, rs, re, red);
+  const int sw_g = jacobi<T>(A, S, m, rc, rs, re, red);
   // 2) S <- Q diag(g)^-1/2, dropping directions with g <= drop_rel gmax
   if (tid == 0) {
     double gmax = 0;
@@ -158,7 +161,8 @@ __global__ void __launch_bounds__(256) k_small_rr(const double2* Gall, const dou
   }
   for (size_t e = tid; e < mm; e += nt) Z[e] = cx<T>((e / m) == (e % m) ? (T)1 : (T)0, 0);
   __syncthreads();
-  jacobi<T>(A, Z, m, rc, rs, re, red);
+  const int sw_h = jacobi<T>(A, Z, m, rc, rs, re, red);
+  if (tid == 0) { dropped[1 + 2 * t] = sw_g; dropped[2 + 2 * t] = sw_h; }
   // 4) sort ascending.  A dropped direction i has an exactly zero row and column
   //    in S^dag H S, so Jacobi never rotates it and it keeps position i: sort it last.
   for (int i = tid; i < m; i += nt) lam[i] = lam[i] > 0 ? (double)A[i * m + i].re : 1e300;

@@ -43,6 +43,8 @@ struct CgScal {
   double* rbest;   // smallest FP64 residual seen at an update
   int* stall;      // consecutive updates without halving rbest
   int* rst;        // restart the search direction at this update (p = r)
+  int* cf;         // mask of the final full-lattice residual evaluation
+  int* exact;      // rnorm comes from an FP64 evaluation of bhat - Dhat x64
   int* count;      // [0] iterating, [1] nonfinite flag, [2] paused for update
 };
 
@@ -251,6 +253,19 @@ __global__ void k_rowsum(const double* part, int nb, int nrhs, double* out, int 
   if (lane == 0) out[j] = do_sqrt ? sqrt(s) : s;
 }
 
+// the paused rhs get their residual from an FP64 evaluation at this update
+__global__ void k_mark_exact(int nrhs, CgScal sc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nrhs && sc.ru[j]) sc.exact[j] = 1;
+}
+
+// rhs whose reported residual still needs an FP64 evaluation on the full lattice:
+// stopped before converging, or retired without an FP64 residual
+__global__ void k_final_mask(int nrhs, CgScal sc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nrhs) sc.cf[j] = sc.alive[j] || !sc.exact[j];
+}
+
 // after the FP64 residual of the paused rhs: retire the converged, mark the rest for resumption
 __global__ void k_ru_check(int nrhs, CgScal sc, double tol) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -334,15 +349,23 @@ static dlma_status reliable_update(dlma_ctx* ctx, SolveBufs& B, int nrhs, double
   const int Vh = ctx->g.Vh;
   const dim3 gv((Vh + BX - 1) / BX, nrhs);
   const int* ru = B.sc.ru;
-  if (!first) {
+  const int nb1 = (nrhs + 127) / 128;
+  if (first) {
+    // x64 = 0: the residual is bhat itself, |bhat| = s
+    CU(cudaMemcpyAsync(B.r64.data, B.bh.data, field_bytes_per_rhs(DLMA_FP64, Vh) * nrhs, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    CU(cudaMemcpyAsync(B.sc.rnorm, B.sc.scale, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
     k_fold<PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (double2*)B.x64.data, B.xl.data, B.sc.scale, ru);
     CHECK_LAUNCH();
+    TRY(schur_apply(ctx, B.x64, B.t64o, B.t64, 0, ru, nullptr));
+    k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.bh.data, (const double2*)B.t64.data,
+                                        (double2*)B.r64.data, ru, B.part2);
+    CHECK_LAUNCH();
+    TRY(rowsum(ctx, B.part2, gv.x, nrhs, B.sc.rnorm, 1, ru));
   }
-  TRY(schur_apply(ctx, B.x64, B.t64o, B.t64, 0, ru, nullptr));
-  k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.bh.data, (const double2*)B.t64.data,
-                                      (double2*)B.r64.data, ru, B.part2);
+  k_mark_exact<<<nb1, 128, 0, ctx->stream>>>(nrhs, B.sc);
   CHECK_LAUNCH();
-  TRY(rowsum(ctx, B.part2, gv.x, nrhs, B.sc.rnorm, 1, ru));
   k_ru_check<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc, tol_target);
   CHECK_LAUNCH();
   const int* upd = B.sc.upd;
@@ -414,7 +437,7 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   double* tmpd = sd + 8 * nrhs;     // 2 nrhs scratch
   TRY(workT(ctx, WS_T0, (size_t)nrhs + 16, &B.sc.rbest));
   int* si;
-  TRY(workT(ctx, WS_ACT, (size_t)10 * nrhs + 16, &si));
+  TRY(workT(ctx, WS_ACT, (size_t)12 * nrhs + 16, &si));
   B.sc.active = si;
   B.sc.alive = si + nrhs;
   B.sc.ru = si + 2 * nrhs;
@@ -424,7 +447,9 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   B.sc.nupd = si + 6 * nrhs;
   B.sc.stall = si + 7 * nrhs;
   B.sc.rst = si + 8 * nrhs;
-  B.sc.count = si + 9 * nrhs;
+  B.sc.cf = si + 9 * nrhs;
+  B.sc.exact = si + 10 * nrhs;
+  B.sc.count = si + 11 * nrhs;
   int* hcount = (int*)ctx->pinned;
 
   const dim3 gv((Vh + BX - 1) / BX, nrhs);
@@ -466,7 +491,8 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   CU(cudaMemcpyAsync(B.sc.bnorm, bn.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
   CU(cudaMemcpyAsync(B.sc.alive, alive0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
   CU(cudaMemcpyAsync(B.sc.ru, alive0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
-  for (int* z : {B.sc.active, B.sc.upd, B.sc.iters, B.sc.since, B.sc.nupd, B.sc.stall, B.sc.rst})
+  for (int* z : {B.sc.active, B.sc.upd, B.sc.iters, B.sc.since, B.sc.nupd, B.sc.stall, B.sc.rst, B.sc.cf,
+                 B.sc.exact})
     CU(cudaMemcpyAsync(z, zeros.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
   std::vector<double> big(nrhs, 1e300);
   CU(cudaMemcpyAsync(B.sc.rbest, big.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
@@ -566,33 +592,42 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   }
   TRY(unpack_parity(ctx, B.x64, 1, 0, x_dev));
   TRY(unpack_parity(ctx, B.t64o, 1, 1, x_dev));
-  // true residual ||b - D x|| / ||b|| on the full lattice in FP64
+  // reported residual ||b - D x|| / ||b||: for an rhs retired on an FP64 residual it is
+  // that residual, |bhat - Dhat x_e| (x_o above makes the odd rows of b - D x vanish);
+  // the rest (stopped early, or retired on a recursive residual) are evaluated on the
+  // full lattice in FP64 here
   {
+    k_final_mask<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc);
+    CHECK_LAUNCH();
+    const int* fm = B.sc.cf;
     Field xe = B.r64;
     CU(cudaMemcpyAsync(xe.data, B.x64.data, field_bytes_per_rhs(DLMA_FP64, Vh) * nrhs, cudaMemcpyDeviceToDevice,
                        ctx->stream));
     HopOp d;
-    d.own = 2; d.kout = 0; d.p_out = 0;
+    d.own = 2; d.kout = 0; d.p_out = 0; d.active = fm;
     TRY(launch_hop(ctx, d, B.t64o, &xe, B.t64));            // (Dx)_e
     k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.b_e.data, (const double2*)B.t64.data,
-                                        (double2*)B.bh.data, nullptr, B.part);
+                                        (double2*)B.bh.data, fm, B.part);
     CHECK_LAUNCH();
-    TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd, 0, nullptr));
+    TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd, 0, fm));
     d.p_out = 1;
     TRY(launch_hop(ctx, d, xe, &B.t64o, B.t64));            // (Dx)_o
     k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.b_o.data, (const double2*)B.t64.data,
-                                        (double2*)B.bh.data, nullptr, B.part);
+                                        (double2*)B.bh.data, fm, B.part);
     CHECK_LAUNCH();
-    TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd + nrhs, 0, nullptr));
-    std::vector<double> h(2 * nrhs);
-    std::vector<int> hit(nrhs), hup(nrhs);
+    TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd + nrhs, 0, fm));
+    std::vector<double> h(2 * nrhs), hr(nrhs);
+    std::vector<int> hit(nrhs), hup(nrhs), hm(nrhs);
     CU(cudaMemcpyAsync(h.data(), tmpd, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(hr.data(), B.sc.rnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(hm.data(), fm, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaMemcpyAsync(hit.data(), B.sc.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaMemcpyAsync(hup.data(), B.sc.nupd, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     bool all = true;
     for (int j = 0; j < nrhs; j++) {
-      const double res = bn[j] > 0 ? sqrt(h[j] + h[nrhs + j]) / bn[j] : 0.0;
+      const double rn = hm[j] ? sqrt(h[j] + h[nrhs + j]) : (alive0[j] ? hr[j] : 0.0);
+      const double res = bn[j] > 0 ? rn / bn[j] : 0.0;
       const int conv = res <= tol;
       all = all && conv;
       if (info) {
