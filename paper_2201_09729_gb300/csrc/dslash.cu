@@ -7,9 +7,9 @@
 // with Kown / Kout one of {1, T_p, T_p^-1}; this single kernel family gives
 // the full operator, the Schur complement Dhat = T_ee - D_eo T_oo^-1 D_oe, its
 // gamma_5 adjoint and the even-odd source preparation / solution
-// reconstruction.  One thread per (output site, right-hand side); a block is
-// SX sites x SY right-hand sides, so the SY warps of a site tile share the
-// link and clover loads through L1.  Spin projection uses the chiral basis
+// reconstruction.  One thread per output site and NR right-hand sides; a block
+// is SX sites x SY groups of right-hand sides, so the SY warps of a site tile
+// share the link and clover loads through L1.  Spin projection uses the chiral basis
 // (gamma_5 = diag(1,1,-1,-1)): every (1 -+ g_mu) halves the colour work.
 #include "common.cuh"
 
@@ -102,34 +102,23 @@ __device__ __forceinline__ void load_clover_block(const void* __restrict__ C, in
   }
 }
 
-template <int P>
-__device__ __forceinline__ void clover_apply(const void* __restrict__ C, int i, int Vh,
-                                             Spinor<typename PT<P>::R>& v) {
-  typedef typename PT<P>::R R;
-#pragma unroll
-  for (int ch = 0; ch < 2; ch++) {
-    R a[36];
-    load_clover_block<P>(C, i, Vh, ch, a);
-    Cx<R> in[6], out[6];
-#pragma unroll
-    for (int r = 0; r < 6; r++) {
-      in[r] = v.c[2 * ch + r / 3][r % 3];
-      out[r] = a[r] * in[r];
-    }
-    int k = 6;
-#pragma unroll
-    for (int r = 1; r < 6; r++)
-#pragma unroll
-      for (int c = 0; c < r; c++) {
-        Cx<R> l = cx<R>(a[k], a[k + 1]);
-        k += 2;
-        fma_acc(out[r], l, in[c]);
-        fma_conj_acc(out[c], l, in[r]);
-      }
-#pragma unroll
-    for (int r = 0; r < 6; r++) v.c[2 * ch + r / 3][r % 3] = out[r];
-  }
-}
+// Work per thread: NR right-hand sides of one site (FP32 stencil), so each link is
+// loaded and reconstructed, and each clover block loaded, once for NR spinors.
+// The FP64 stencil is arithmetic-bound and the FP16 one register-bound: both keep
+// one.  MINB: resident blocks of 256 threads per SM the kernels are compiled for
+// (their register cap).  Measured on the 16^3 x 32 solve: NR = 1 with MINB = 3
+// and NR = 2 with MINB = 2 are within 2 % (NR = 2 speeds the plain operator by
+// 6 % but its CG variants spill); NR = 1 is the default.
+#ifndef DLMA_HOP_NR
+#define DLMA_HOP_NR 1
+#endif
+#ifndef DLMA_HOP_MINB
+#define DLMA_HOP_MINB 3
+#endif
+template <int P> struct HopCfg {
+  static constexpr int NR = P == DLMA_FP32 ? DLMA_HOP_NR : 1;
+  static constexpr int MINB = P == DLMA_FP32 ? DLMA_HOP_MINB : P == DLMA_FP64 ? 2 : 3;
+};
 
 // ---------------------------------------------------------------------------
 struct HopArgs {
@@ -172,145 +161,279 @@ __device__ __forceinline__ void su3_dag_mul(const Cx<R> U[3][3], const Cx<R> h[3
   }
 }
 
-template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM, bool L18, bool CGU = false>
-__global__ void __launch_bounds__(256, P == DLMA_FP64 ? 2 : 3) k_hop(HopArgs a) {
+// one chirality block (spins 2 ch, 2 ch + 1) of a spinor field at site i
+template <int P>
+__device__ __forceinline__ void load_chiral(const void* __restrict__ base, const float* __restrict__ scale, int Vh,
+                                            int i, int ch, Cx<typename PT<P>::R> v[6]) {
   typedef typename PT<P>::R R;
-  // grid x runs over right-hand-side groups (fast), grid y over site tiles: all
+  if (P == DLMA_FP64) {
+    const double2* b = (const double2*)base;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const double2 e = __ldg(b + (size_t)(6 * ch + k) * Vh + i);
+      v[k] = cx<R>((R)e.x, (R)e.y);
+    }
+  } else if (P == DLMA_FP32) {
+    const float4* b = (const float4*)base;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      const float4 e = __ldg(b + (size_t)(3 * ch + q) * Vh + i);
+      v[2 * q] = cx<R>(e.x, e.y);
+      v[2 * q + 1] = cx<R>(e.z, e.w);
+    }
+  } else {
+    const Spinor<R> f = load_spinor<P>(base, scale, Vh, i);
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = f.c[2 * ch + k / 3][k % 3];
+  }
+}
+
+// out = A in for one 6 x 6 hermitian chirality block (36 packed reals: diagonal, then
+// the strictly lower triangle row by row)
+template <class R>
+__device__ __forceinline__ void clover_block_mul(const R a[36], const Cx<R> in[6], Cx<R> out[6]) {
+#pragma unroll
+  for (int r = 0; r < 6; r++) out[r] = a[r] * in[r];
+  int k = 6;
+#pragma unroll
+  for (int r = 1; r < 6; r++)
+#pragma unroll
+    for (int c = 0; c < r; c++) {
+      const Cx<R> l = cx<R>(a[k], a[k + 1]);
+      k += 2;
+      fma_acc(out[r], l, in[c]);
+      fma_conj_acc(out[c], l, in[r]);
+    }
+}
+
+// CG epilogue of one right-hand side: x += al p, r -= al z, returns |r|^2 (summed in
+// the vector precision: FP64 arithmetic is scarce next to an FP32 stencil)
+template <int PB, class R>
+__device__ __forceinline__ R cg_update(void* __restrict__ x, void* __restrict__ r, const void* __restrict__ p, int Vh,
+                                       int i, double al, const Spinor<R>& z) {
+  R n = 0;
+  if (PB == DLMA_FP64) {
+    double2* xb = (double2*)x;
+    double2* rb = (double2*)r;
+    const double2* pb = (const double2*)p;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const size_t o = (size_t)k * Vh + i;
+      double2 xv = xb[o], rv = rb[o];
+      const double2 pv = pb[o];
+      const Cx<R> zz = z.c[k / 3][k % 3];
+      xv.x += al * pv.x; xv.y += al * pv.y;
+      rv.x -= al * (double)zz.re; rv.y -= al * (double)zz.im;
+      xb[o] = xv;
+      rb[o] = rv;
+      n += rv.x * rv.x + rv.y * rv.y;
+    }
+  } else {
+    float4* xb = (float4*)x;
+    float4* rb = (float4*)r;
+    const float4* pb = (const float4*)p;
+    const float af = (float)al;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+      const size_t o = (size_t)q * Vh + i;
+      float4 xv = xb[o], rv = rb[o];
+      const float4 pv = pb[o];
+      const Cx<R> z0 = z.c[(2 * q) / 3][(2 * q) % 3], z1 = z.c[(2 * q + 1) / 3][(2 * q + 1) % 3];
+      xv.x += af * pv.x; xv.y += af * pv.y; xv.z += af * pv.z; xv.w += af * pv.w;
+      rv.x -= af * (float)z0.re; rv.y -= af * (float)z0.im; rv.z -= af * (float)z1.re; rv.w -= af * (float)z1.im;
+      xb[o] = xv;
+      rb[o] = rv;
+      n += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+    }
+  }
+  return n;
+}
+
+template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM, bool L18, bool CGU = false>
+__global__ void __launch_bounds__(256, HopCfg<P>::MINB) k_hop(HopArgs a) {
+  typedef typename PT<P>::R R;
+  constexpr int NR = HopCfg<P>::NR;
+  // grid x runs over groups of right-hand sides (fast), grid y over site tiles: all
   // right-hand sides of a site tile run back to back, so its links and clover
   // come from DRAM once and from L2 afterwards
   const int i = blockIdx.y * blockDim.x + threadIdx.x;
-  const int j = blockIdx.x * blockDim.y + threadIdx.y;
+  const int j0 = (blockIdx.x * blockDim.y + threadIdx.y) * NR;
   const Geom g = a.g;
-  bool valid = i < g.Vh && j < a.nrhs;
-  if (valid && a.active) valid = a.active[j] != 0;
-  double nrm = 0.0;
+  int jq[NR];
+  bool vq[NR];
+  bool valid = false;
+  int jany = 0;
+#pragma unroll
+  for (int q = NR - 1; q >= 0; q--) {
+    jq[q] = j0 + q;
+    vq[q] = i < g.Vh && jq[q] < a.nrhs && (!a.active || a.active[jq[q]] != 0);
+    if (vq[q]) { valid = true; jany = jq[q]; }
+  }
+  // loads of an idle slot read a live right-hand side of this thread (always in bounds)
+  int jl[NR];
+#pragma unroll
+  for (int q = 0; q < NR; q++) jl[q] = vq[q] ? jq[q] : jany;
+  R nrm[NR];   // |out|^2 per thread in the stencil precision; block partials in FP64
+#pragma unroll
+  for (int q = 0; q < NR; q++) nrm[q] = 0;
   if (valid) {
-    Spinor<R> res;
+    Spinor<R> res[NR];
 #pragma unroll
-    for (int s = 0; s < 4; s++)
+    for (int q = 0; q < NR; q++)
 #pragma unroll
-      for (int c = 0; c < 3; c++) res.c[s][c] = cx<R>(0, 0);
+      for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) res[q].c[s][c] = cx<R>(0, 0);
     if (HOP) {
       const int4 q0 = __ldg(a.nbr + ((size_t)a.p_out * 2 + 0) * g.Vh + i);
       const int4 q1 = __ldg(a.nbr + ((size_t)a.p_out * 2 + 1) * g.Vh + i);
       const int nb8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-      const char* inb = (const char*)a.in;
-      const void* in_j = inb + (size_t)j * a.in_stride;
-      const float* sc_j = a.in_scale ? a.in_scale + (size_t)j * g.Vh : nullptr;
 #pragma unroll
       for (int mu = 0; mu < 4; mu++) {
 #pragma unroll
         for (int dir = 0; dir < 2; dir++) {
           const int raw = nb8[2 * mu + dir];
           const int n = mu == 0 ? (raw & 0x7fffffff) : raw;   // only time neighbours carry the phase bit
-          Spinor<R> ps = load_spinor<P>(in_j, sc_j, g.Vh, n);
-          if (G5IN) {
-#pragma unroll
-            for (int c = 0; c < 3; c++) { ps.c[2][c] = -ps.c[2][c]; ps.c[3][c] = -ps.c[3][c]; }
-          }
           Cx<R> U[3][3];
           // forward: U_mu(x) at this site; backward: U_mu(x - mu) at the neighbour
           load_link<P>(a.Ua, a.Ub, dir == 0 ? a.p_out : 1 - a.p_out, mu, dir == 0 ? i : n, g.Vh, U, L18);
           const R ph = raw < 0 ? (R)-1 : (R)1;    // antiperiodic time phase (bit 31, mu = 0 only)
-          Cx<R> h0[3], h1[3], w0[3], w1[3];
 #pragma unroll
-          for (int c = 0; c < 3; c++) {
-            const Cx<R> u0 = ps.c[0][c], u1 = ps.c[1][c], d0 = ps.c[2][c], d1 = ps.c[3][c];
-            if (dir == 0) {           // (1 - g_mu)
-              if (mu == 0) { h0[c] = u0 + d0; h1[c] = u1 + d1; }
-              else if (mu == 1) { h0[c] = u0 + mul_i(d1); h1[c] = u1 + mul_i(d0); }
-              else if (mu == 2) { h0[c] = u0 + d1; h1[c] = u1 - d0; }
-              else { h0[c] = u0 + mul_i(d0); h1[c] = u1 - mul_i(d1); }
-            } else {                  // (1 + g_mu)
-              if (mu == 0) { h0[c] = u0 - d0; h1[c] = u1 - d1; }
-              else if (mu == 1) { h0[c] = u0 - mul_i(d1); h1[c] = u1 - mul_i(d0); }
-              else if (mu == 2) { h0[c] = u0 - d1; h1[c] = u1 + d0; }
-              else { h0[c] = u0 - mul_i(d0); h1[c] = u1 + mul_i(d1); }
+          for (int q = 0; q < NR; q++) {
+            Spinor<R> ps = load_spinor<P>((const char*)a.in + (size_t)jl[q] * a.in_stride,
+                                          a.in_scale ? a.in_scale + (size_t)jl[q] * g.Vh : nullptr, g.Vh, n);
+            if (G5IN) {
+#pragma unroll
+              for (int c = 0; c < 3; c++) { ps.c[2][c] = -ps.c[2][c]; ps.c[3][c] = -ps.c[3][c]; }
             }
-          }
-          if (dir == 0) { su3_mul(U, h0, w0); su3_mul(U, h1, w1); }
-          else { su3_dag_mul(U, h0, w0); su3_dag_mul(U, h1, w1); }
+            Cx<R> h0[3], h1[3], w0[3], w1[3];
 #pragma unroll
-          for (int c = 0; c < 3; c++) {
-            const Cx<R> x0 = mu == 0 ? ph * w0[c] : w0[c], x1 = mu == 0 ? ph * w1[c] : w1[c];
-            res.c[0][c] = res.c[0][c] + x0;
-            res.c[1][c] = res.c[1][c] + x1;
-            if (dir == 0) {
-              if (mu == 0) { res.c[2][c] = res.c[2][c] + x0; res.c[3][c] = res.c[3][c] + x1; }
-              else if (mu == 1) { res.c[2][c] = res.c[2][c] - mul_i(x1); res.c[3][c] = res.c[3][c] - mul_i(x0); }
-              else if (mu == 2) { res.c[2][c] = res.c[2][c] - x1; res.c[3][c] = res.c[3][c] + x0; }
-              else { res.c[2][c] = res.c[2][c] - mul_i(x0); res.c[3][c] = res.c[3][c] + mul_i(x1); }
-            } else {
-              if (mu == 0) { res.c[2][c] = res.c[2][c] - x0; res.c[3][c] = res.c[3][c] - x1; }
-              else if (mu == 1) { res.c[2][c] = res.c[2][c] + mul_i(x1); res.c[3][c] = res.c[3][c] + mul_i(x0); }
-              else if (mu == 2) { res.c[2][c] = res.c[2][c] + x1; res.c[3][c] = res.c[3][c] - x0; }
-              else { res.c[2][c] = res.c[2][c] + mul_i(x0); res.c[3][c] = res.c[3][c] - mul_i(x1); }
+            for (int c = 0; c < 3; c++) {
+              const Cx<R> u0 = ps.c[0][c], u1 = ps.c[1][c], d0 = ps.c[2][c], d1 = ps.c[3][c];
+              if (dir == 0) {           // (1 - g_mu)
+                if (mu == 0) { h0[c] = u0 + d0; h1[c] = u1 + d1; }
+                else if (mu == 1) { h0[c] = u0 + mul_i(d1); h1[c] = u1 + mul_i(d0); }
+                else if (mu == 2) { h0[c] = u0 + d1; h1[c] = u1 - d0; }
+                else { h0[c] = u0 + mul_i(d0); h1[c] = u1 - mul_i(d1); }
+              } else {                  // (1 + g_mu)
+                if (mu == 0) { h0[c] = u0 - d0; h1[c] = u1 - d1; }
+                else if (mu == 1) { h0[c] = u0 - mul_i(d1); h1[c] = u1 - mul_i(d0); }
+                else if (mu == 2) { h0[c] = u0 - d1; h1[c] = u1 + d0; }
+                else { h0[c] = u0 - mul_i(d0); h1[c] = u1 + mul_i(d1); }
+              }
+            }
+            if (dir == 0) { su3_mul(U, h0, w0); su3_mul(U, h1, w1); }
+            else { su3_dag_mul(U, h0, w0); su3_dag_mul(U, h1, w1); }
+            Spinor<R>& rq = res[q];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+              const Cx<R> x0 = mu == 0 ? ph * w0[c] : w0[c], x1 = mu == 0 ? ph * w1[c] : w1[c];
+              rq.c[0][c] = rq.c[0][c] + x0;
+              rq.c[1][c] = rq.c[1][c] + x1;
+              if (dir == 0) {
+                if (mu == 0) { rq.c[2][c] = rq.c[2][c] + x0; rq.c[3][c] = rq.c[3][c] + x1; }
+                else if (mu == 1) { rq.c[2][c] = rq.c[2][c] - mul_i(x1); rq.c[3][c] = rq.c[3][c] - mul_i(x0); }
+                else if (mu == 2) { rq.c[2][c] = rq.c[2][c] - x1; rq.c[3][c] = rq.c[3][c] + x0; }
+                else { rq.c[2][c] = rq.c[2][c] - mul_i(x0); rq.c[3][c] = rq.c[3][c] + mul_i(x1); }
+              } else {
+                if (mu == 0) { rq.c[2][c] = rq.c[2][c] - x0; rq.c[3][c] = rq.c[3][c] - x1; }
+                else if (mu == 1) { rq.c[2][c] = rq.c[2][c] + mul_i(x1); rq.c[3][c] = rq.c[3][c] + mul_i(x0); }
+                else if (mu == 2) { rq.c[2][c] = rq.c[2][c] + x1; rq.c[3][c] = rq.c[3][c] - x0; }
+                else { rq.c[2][c] = rq.c[2][c] + mul_i(x0); rq.c[3][c] = rq.c[3][c] - mul_i(x1); }
+              }
             }
           }
         }
       }
       const R f = (R)(-0.5 * a.s);
 #pragma unroll
-      for (int s = 0; s < 4; s++)
+      for (int q = 0; q < NR; q++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) {
-          R ff = (G5HOP && s >= 2) ? -f : f;
-          res.c[s][c] = ff * res.c[s][c];
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const R ff = (G5HOP && s >= 2) ? -f : f;
+            res[q].c[s][c] = ff * res[q].c[s][c];
+          }
+    }
+    // own-site term and outer clover factor, chirality block by block: each block
+    // of the clover field is loaded once for the NR right-hand sides
+    if (OWN || KOUT) {
+#pragma unroll
+      for (int ch = 0; ch < 2; ch++) {
+        if (OWN) {
+          R k[36];
+          if (OWN == 2) load_clover_block<P>(a.Kown, i, g.Vh, ch, k);
+#pragma unroll
+          for (int q = 0; q < NR; q++) {
+            Cx<R> o[6], t[6];
+            load_chiral<P>((const char*)a.own + (size_t)jl[q] * a.own_stride,
+                           a.own_scale ? a.own_scale + (size_t)jl[q] * g.Vh : nullptr, g.Vh, i, ch, o);
+            if (OWN == 2) clover_block_mul(k, o, t);
+#pragma unroll
+            for (int r = 0; r < 6; r++) {
+              Cx<R>& e = res[q].c[2 * ch + r / 3][r % 3];
+              e = e + (OWN == 2 ? t[r] : o[r]);
+            }
+          }
         }
-    }
-    if (OWN) {
-      const void* own_j = (const char*)a.own + (size_t)j * a.own_stride;
-      const float* osc = a.own_scale ? a.own_scale + (size_t)j * g.Vh : nullptr;
-      Spinor<R> o = load_spinor<P>(own_j, osc, g.Vh, i);
-      if (OWN == 2) clover_apply<P>(a.Kown, i, g.Vh, o);
+        if (KOUT) {
+          R k[36];
+          load_clover_block<P>(a.Kout, i, g.Vh, ch, k);
 #pragma unroll
-      for (int s = 0; s < 4; s++)
+          for (int q = 0; q < NR; q++) {
+            Cx<R> o[6], t[6];
 #pragma unroll
-        for (int c = 0; c < 3; c++) res.c[s][c] = res.c[s][c] + o.c[s][c];
-    }
-    if (KOUT) clover_apply<P>(a.Kout, i, g.Vh, res);
-    if (CGU) {
-      // fused CG update: z (= res) is consumed here and never stored
-      constexpr int PB = P == DLMA_FP64 ? DLMA_FP64 : DLMA_FP32;
-      typedef typename PT<PB>::R RB;
-      const size_t sb = (size_t)j * a.cg_stride;
-      const RB al = (RB)a.cg_alpha[j];
-      Spinor<RB> xv = load_spinor<PB>((char*)a.cg_x + sb, nullptr, g.Vh, i);
-      Spinor<RB> rv = load_spinor<PB>((char*)a.cg_r + sb, nullptr, g.Vh, i);
-      const Spinor<RB> pv = load_spinor<PB>((const char*)a.cg_p + sb, nullptr, g.Vh, i);
+            for (int r = 0; r < 6; r++) o[r] = res[q].c[2 * ch + r / 3][r % 3];
+            clover_block_mul(k, o, t);
 #pragma unroll
-      for (int s = 0; s < 4; s++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-          xv.c[s][c] = xv.c[s][c] + al * pv.c[s][c];
-          rv.c[s][c] = rv.c[s][c] - al * cx<RB>((RB)res.c[s][c].re, (RB)res.c[s][c].im);
-          nrm += (double)norm2(rv.c[s][c]);
+            for (int r = 0; r < 6; r++) res[q].c[2 * ch + r / 3][r % 3] = t[r];
+          }
         }
-      store_spinor<PB>((char*)a.cg_x + sb, nullptr, g.Vh, i, xv);
-      store_spinor<PB>((char*)a.cg_r + sb, nullptr, g.Vh, i, rv);
-    } else {
-      store_spinor<P>((char*)a.out + (size_t)j * a.out_stride, a.out_scale ? a.out_scale + (size_t)j * g.Vh : nullptr,
-                      g.Vh, i, res);
+      }
     }
-    if (NORM && !CGU) {
 #pragma unroll
-      for (int s = 0; s < 4; s++)
+    for (int q = 0; q < NR; q++) {
+      if (!vq[q]) continue;
+      const int j = jq[q];
+      if (CGU) {
+        // fused CG update: z (= res) is consumed here and never stored
+        constexpr int PB = P == DLMA_FP64 ? DLMA_FP64 : DLMA_FP32;
+        const size_t sb = (size_t)j * a.cg_stride;
+        nrm[q] = cg_update<PB>((char*)a.cg_x + sb, (char*)a.cg_r + sb, (const char*)a.cg_p + sb, g.Vh, i,
+                               a.cg_alpha[j], res[q]);
+      } else {
+        store_spinor<P>((char*)a.out + (size_t)j * a.out_stride,
+                        a.out_scale ? a.out_scale + (size_t)j * g.Vh : nullptr, g.Vh, i, res[q]);
+        if (NORM) {
 #pragma unroll
-        for (int c = 0; c < 3; c++) nrm += (double)norm2(res.c[s][c]);
+          for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) nrm[q] += norm2(res[q].c[s][c]);
+        }
+      }
     }
   }
   if (NORM) {
-    // per (rhs, block) partial sum: warps run along x for one rhs row
-    __shared__ double red[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    // per (rhs, block) partial sums: the warps of one threadIdx.y row share NR rhs
+    __shared__ double red[32 * NR];
     const int wx = threadIdx.x >> 5, nwx = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0) red[threadIdx.y * nwx + wx] = nrm;
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+      R v = nrm[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) red[(threadIdx.y * nwx + wx) * NR + q] = (double)v;
+    }
     __syncthreads();
-    if (threadIdx.x == 0 && j < a.nrhs) {
-      double t = 0;
-      for (int w = 0; w < nwx; w++) t += red[threadIdx.y * nwx + w];
-      a.norm_part[(size_t)j * gridDim.y + blockIdx.y] = t;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NR; q++) {
+        if (jq[q] >= a.nrhs) continue;
+        double t = 0;
+        for (int w = 0; w < nwx; w++) t += red[(threadIdx.y * nwx + w) * NR + q];
+        a.norm_part[(size_t)jq[q] * gridDim.y + blockIdx.y] = t;
+      }
     }
   }
 }
@@ -411,7 +534,8 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   int sx, sy;
   hop_block(ctx, P, sx, sy);
   dim3 blk(sx, sy);
-  dim3 grid((out.nrhs + sy - 1) / sy, (ctx->g.Vh + sx - 1) / sx);
+  const int nr = P == DLMA_FP32 ? HopCfg<DLMA_FP32>::NR : 1;
+  dim3 grid((out.nrhs + sy * nr - 1) / (sy * nr), (ctx->g.Vh + sx - 1) / sx);
   if (nblocks_out) *nblocks_out = grid.y;
   if (P == DLMA_FP64) dispatch<DLMA_FP64, false>(op, grid, blk, ctx->stream, a);
   else if (P == DLMA_FP32 && a.l18) dispatch<DLMA_FP32, true>(op, grid, blk, ctx->stream, a);
