@@ -115,6 +115,12 @@ __device__ __forceinline__ void load_clover_block(const void* __restrict__ C, in
 #ifndef DLMA_HOP_MINB
 #define DLMA_HOP_MINB 3
 #endif
+// right-hand sides per chunk of the block order (see k_hop); on the 16^3 x 32 solve
+// 64 measured best of {16, 32, 64, unchunked}
+#ifndef DLMA_HOP_CHUNK
+#define DLMA_HOP_CHUNK 64
+#endif
+constexpr int kHopChunkRhs = DLMA_HOP_CHUNK;
 template <int P> struct HopCfg {
   static constexpr int NR = P == DLMA_FP32 ? DLMA_HOP_NR : 1;
   static constexpr int MINB = P == DLMA_FP32 ? DLMA_HOP_MINB : P == DLMA_FP64 ? 2 : 3;
@@ -137,6 +143,9 @@ struct HopArgs {
   // CG epilogue (CGU): with z the result at this site, x += alpha p, r -= alpha z
   // (vector precision PB = FP64 for an FP64 stencil, FP32 otherwise), partial |r|^2
   void* cg_x; void* cg_r; const void* cg_p; const double* cg_alpha; size_t cg_stride;
+  // block order (1D grid): chunks of right-hand-side groups (slowest), site tiles,
+  // groups within the chunk (fastest)
+  int ntiles, ngroups, gpc;
 };
 
 template <class R>
@@ -253,11 +262,16 @@ template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM,
 __global__ void __launch_bounds__(256, HopCfg<P>::MINB) k_hop(HopArgs a) {
   typedef typename PT<P>::R R;
   constexpr int NR = HopCfg<P>::NR;
-  // grid x runs over groups of right-hand sides (fast), grid y over site tiles: all
-  // right-hand sides of a site tile run back to back, so its links and clover
-  // come from DRAM once and from L2 afterwards
-  const int i = blockIdx.y * blockDim.x + threadIdx.x;
-  const int j0 = (blockIdx.x * blockDim.y + threadIdx.y) * NR;
+  // Block order: the right-hand sides of a chunk (gpc groups, about 32 rhs) run back
+  // to back on a site tile, so its links and clover come from DRAM once per chunk
+  // and from L2 otherwise; the chunk sweeps all tiles before the next chunk starts,
+  // which keeps the neighbour spinors in flight (+-t is 2 L^3 / 2 sites away) within
+  // L2.  Blocks past the last group have no valid thread.
+  const int per_chunk = a.ntiles * a.gpc;
+  const int chunk = blockIdx.x / per_chunk, rem = blockIdx.x - chunk * per_chunk;
+  const int tile = rem / a.gpc, grp = chunk * a.gpc + (rem - (rem / a.gpc) * a.gpc);
+  const int i = tile * blockDim.x + threadIdx.x;
+  const int j0 = (grp * blockDim.y + threadIdx.y) * NR;
   const Geom g = a.g;
   int jq[NR];
   bool vq[NR];
@@ -432,7 +446,7 @@ __global__ void __launch_bounds__(256, HopCfg<P>::MINB) k_hop(HopArgs a) {
         if (jq[q] >= a.nrhs) continue;
         double t = 0;
         for (int w = 0; w < nwx; w++) t += red[(threadIdx.y * nwx + w) * NR + q];
-        a.norm_part[(size_t)jq[q] * gridDim.y + blockIdx.y] = t;
+        a.norm_part[(size_t)jq[q] * a.ntiles + tile] = t;
       }
     }
   }
@@ -535,8 +549,12 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   hop_block(ctx, P, sx, sy);
   dim3 blk(sx, sy);
   const int nr = P == DLMA_FP32 ? HopCfg<DLMA_FP32>::NR : 1;
-  dim3 grid((out.nrhs + sy * nr - 1) / (sy * nr), (ctx->g.Vh + sx - 1) / sx);
-  if (nblocks_out) *nblocks_out = grid.y;
+  a.ntiles = (ctx->g.Vh + sx - 1) / sx;
+  a.ngroups = (out.nrhs + sy * nr - 1) / (sy * nr);
+  a.gpc = std::max(1, std::min(a.ngroups, kHopChunkRhs / (sy * nr)));
+  const int nchunks = (a.ngroups + a.gpc - 1) / a.gpc;
+  dim3 grid((unsigned)((size_t)nchunks * a.ntiles * a.gpc));
+  if (nblocks_out) *nblocks_out = a.ntiles;
   if (P == DLMA_FP64) dispatch<DLMA_FP64, false>(op, grid, blk, ctx->stream, a);
   else if (P == DLMA_FP32 && a.l18) dispatch<DLMA_FP32, true>(op, grid, blk, ctx->stream, a);
   else if (P == DLMA_FP32) dispatch<DLMA_FP32, false>(op, grid, blk, ctx->stream, a);
