@@ -75,10 +75,16 @@ __global__ void k_transpose_V(const double2* __restrict__ V, int st_t, int st_k,
 }
 
 // coeff[j][t][alpha][k] = sum_{m,c} conj(V_t[k][m][c]) psi_j(site0(t) + m, alpha, c)
+// Block (ntk, KW): threadIdx.x = mode k, threadIdx.y = a slice m = y, y + KW, ... of the
+// timeslice's sites (the sum is split over KW warps so that enough warps keep the
+// FP64 pipes busy), JB right-hand sides per block; the KW partial sums meet in
+// shared memory.
 constexpr int JB = 4;
 __global__ void k_project(const double2* __restrict__ VT, int N, int Vs, int Tsel, const double2* __restrict__ psi,
                           size_t psi_stride_sites, int site_t0, int nrhs, double2* coeff) {
-  const int t = blockIdx.x, j0 = blockIdx.y * JB, k = threadIdx.x;
+  extern __shared__ double2 pred[];   // [KW - 1][JB * 4][ntk]
+  const int t = blockIdx.x, j0 = blockIdx.y * JB, k = threadIdx.x, w = threadIdx.y;
+  const int KW = blockDim.y, ntk = blockDim.x;
   const bool on = k < N;
   Cx<double> acc[JB][4];
 #pragma unroll
@@ -87,7 +93,7 @@ __global__ void k_project(const double2* __restrict__ VT, int N, int Vs, int Tse
     for (int a = 0; a < 4; a++) acc[jj][a] = cx<double>(0, 0);
   const double2* vt = VT + (size_t)t * 3 * Vs * N;
   const size_t site0 = (size_t)(site_t0 + t) * Vs;
-  for (int m = 0; m < Vs; m++) {
+  for (int m = w; m < Vs; m += KW) {
     Cx<double> v[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -107,13 +113,28 @@ __global__ void k_project(const double2* __restrict__ VT, int N, int Vs, int Tse
         }
     }
   }
-  if (!on) return;
+  if (w > 0) {
+#pragma unroll
+    for (int jj = 0; jj < JB; jj++)
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+        pred[((size_t)(w - 1) * JB * 4 + jj * 4 + a) * ntk + k] = make_double2(acc[jj][a].re, acc[jj][a].im);
+  }
+  __syncthreads();
+  if (w != 0 || !on) return;
 #pragma unroll
   for (int jj = 0; jj < JB; jj++) {
     if (j0 + jj >= nrhs) break;
 #pragma unroll
-    for (int a = 0; a < 4; a++)
-      coeff[(((size_t)(j0 + jj) * Tsel + t) * 4 + a) * N + k] = make_double2(acc[jj][a].re, acc[jj][a].im);
+    for (int a = 0; a < 4; a++) {
+      Cx<double> s = acc[jj][a];
+      for (int q = 1; q < KW; q++) {
+        const double2 e = pred[((size_t)(q - 1) * JB * 4 + jj * 4 + a) * ntk + k];
+        s.re += e.x;
+        s.im += e.y;
+      }
+      coeff[(((size_t)(j0 + jj) * Tsel + t) * 4 + a) * N + k] = make_double2(s.re, s.im);
+    }
   }
 }
 
@@ -306,10 +327,14 @@ static dlma_status transpose_V(dlma_ctx* ctx, const double* V, int st_t, int st_
 static dlma_status project(dlma_ctx* ctx, const double2* VT, int N, int Tsel, const double* psi, size_t stride_sites,
                            int site_t0, int nrhs, double2* coeff) {
   if (N > 256) return set_err(ctx, DLMA_ERR_INVALID_ARG, "N above 256 in the projection");
-  int nt = ((N + 31) / 32) * 32;
+  const int nt = ((N + 31) / 32) * 32;
+  // warps splitting the site sum: at most 4, partial sums within 40 KB of shared memory
+  int kw = 4;
+  while (kw > 1 && ((size_t)(kw - 1) * JB * 4 * nt * 16 > 40 * 1024 || nt * kw > 256)) kw--;
+  const size_t smem = (size_t)(kw - 1) * JB * 4 * nt * 16;
   dim3 grid(Tsel, (nrhs + JB - 1) / JB);
-  k_project<<<grid, nt, 0, ctx->stream>>>(VT, N, ctx->g.Vs, Tsel, (const double2*)psi, stride_sites, site_t0, nrhs,
-                                          coeff);
+  k_project<<<grid, dim3(nt, kw), smem, ctx->stream>>>(VT, N, ctx->g.Vs, Tsel, (const double2*)psi, stride_sites,
+                                                      site_t0, nrhs, coeff);
   CHECK_LAUNCH();
   return DLMA_OK;
 }

@@ -61,20 +61,22 @@ __global__ void __launch_bounds__(256) k_lap(Geom g, int t0, int Tn, int m, cons
                                              const Cx<R>* __restrict__ in, const Cx<R>* __restrict__ prev,
                                              const Cx<float>* __restrict__ rin, const double* __restrict__ scol,
                                              Cx<R>* __restrict__ out, const double* __restrict__ coef) {
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t total = (size_t)Tn * g.Vs * m;
+  // 32-bit index arithmetic (the host keeps Tn Vs m below 2^31): 64-bit divisions
+  // would cost more than the stencil's arithmetic
+  const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned total = (unsigned)Tn * (unsigned)g.Vs * (unsigned)m;
   if (e >= total) return;
-  const int j = e % m;
-  const size_t sl = e / m;
-  const int tl = sl / g.Vs;
-  const int ms = sl - (size_t)tl * g.Vs;
+  const unsigned sl = e / (unsigned)m;
+  const int j = (int)(e - sl * (unsigned)m);
+  const int tl = (int)(sl / (unsigned)g.Vs);
+  const int ms = (int)(sl - (unsigned)tl * (unsigned)g.Vs);
   const R alpha = (R)coef[3 * tl], beta = (R)coef[3 * tl + 1], gamma = (R)coef[3 * tl + 2];
   const size_t rowbase = (size_t)tl * g.Vs;
   Cx<R> res[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) res[a] = cx<R>(0, 0);
   if (in) {
-    const int x = ms % g.L, y = (ms / g.L) % g.L, z = ms / (g.L * g.L);
+    const int yz = ms / g.L, x = ms - yz * g.L, z = yz / g.L, y = yz - z * g.L;
     const size_t s = (size_t)(t0 + tl) * g.Vs + ms;
     Cx<R> own[3], acc[3];
 #pragma unroll
@@ -293,8 +295,9 @@ __global__ void k_combine(const Cx<double>* __restrict__ X, const Cx<float>* __r
                           const double* __restrict__ scol, size_t nm, int m, size_t total, Cx<double>* Y) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= total) return;
-  const int j = e % m;
-  const size_t t = e / nm;
+  const unsigned e32 = (unsigned)e;           // total < 2^31 (checked with the block)
+  const int j = (int)(e32 % (unsigned)m);
+  const unsigned t = e32 / (unsigned)nm;
   const double s = scol[t * m + j];
   const Cx<float> ev = E[e];
   Y[e] = s * X[e] + cx<double>((double)ev.re, (double)ev.im);
@@ -407,6 +410,7 @@ static dlma_status lap(Eig& E, const Cx<R>* in, const Cx<R>* prev, const Cx<floa
                        Cx<R>* out, const double* coef) {
   dlma_ctx* ctx = E.ctx;
   const size_t total = (size_t)E.Tn * ctx->g.Vs * E.m;
+  if (total >= (1ull << 31)) return set_err(ctx, DLMA_ERR_INVALID_ARG, "eigensolver block above 2^31 entries");
   k_lap<R><<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(ctx->g, E.t0, E.Tn, E.m, links<R>(ctx), in, prev,
                                                                      rin, scol, out, coef);
   CHECK_LAUNCH();
@@ -436,7 +440,7 @@ template <class R> static dlma_status rotate(Eig& E, const Cx<R>* X, Cx<R>* Z) {
 // small Rayleigh-Ritz problems in precision T (float in phase A, double in phase B)
 template <class T> static dlma_status small_rr(Eig& E) {
   dlma_ctx* ctx = E.ctx;
-  const size_t sm = (size_t)3 * E.m * E.m * sizeof(Cx<T>);
+  const size_t sm = (size_t)3 * E.m * (E.m + 1) * sizeof(Cx<T>);   // three m x (m + 1) work matrices
   // the kernel also holds ~11 KB of static shared memory: always raise the dynamic limit
   const int use_smem = sm <= 200 * 1024;
   if (use_smem) CU(cudaFuncSetAttribute(k_small_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -592,6 +596,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   E.m = m;
   E.degree = 40;            // largest filter degree (phase B); phase A stays below 20
   E.blk = (size_t)m * Tn * E.n;
+  if (E.blk >= (1ull << 31)) return set_err(ctx, DLMA_ERR_INVALID_ARG, "eigensolver block above 2^31 entries");
   E.nsplit = std::max(1, std::min(64, (4 * 152) / std::max(1, Tn * ((m + GT - 1) / GT) * ((m + GT - 1) / GT))));
   E.nsplit = std::min(E.nsplit, std::max(1, E.n / 256));
   TRY(workT(ctx, WS_EIG_X, E.blk * 2, &E.F0));
@@ -606,7 +611,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   E.H = E.G + mm * Tn;
   E.C = E.H + mm * Tn;
   TRY(workT(ctx, WS_EIG_PART, (size_t)E.nsplit * mm * Tn, &E.part));
-  TRY(workT(ctx, WS_EIG_S, 3 * mm * Tn, &E.gwork));
+  TRY(workT(ctx, WS_EIG_S, 3 * (size_t)m * (m + 1) * Tn, &E.gwork));
   const int d = E.degree;
   double* aux;
   const size_t ncoef = (size_t)(d + 1) * 3 * Tn, nscol = (size_t)(d + 1) * Tn * m;

@@ -21,18 +21,20 @@ template <> struct SmallPrec<double> { static constexpr double eps = 1e-15; };
 
 __device__ __forceinline__ int rr_pos(int idx, int r, int m) { return idx == 0 ? 0 : ((idx - 1 + r) % (m - 1)) + 1; }
 
-// Diagonalise the hermitian A [m][m] (row-major, in place), accumulating the
-// rotations into the columns of V (which holds the initial basis).  Returns the
-// number of sweeps.
+// Diagonalise the hermitian A [m][m] (row-major with leading dimension ld, in
+// place), accumulating the rotations into the columns of V (which holds the
+// initial basis).  ld = m + 1 keeps the column updates, where consecutive threads
+// walk down a column, free of shared-memory bank conflicts.  Returns the number
+// of sweeps.
 template <class T>
-__device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, double* red) {
+__device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, int ld, T* rc, T* rs, Cx<T>* re, double* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int np = m / 2;
   __shared__ int rotated;
   __shared__ double dmax;
   if (tid == 0) {
     double mx = 0;
-    for (int i = 0; i < m; i++) mx = fmax(mx, fabs((double)A[i * m + i].re));
+    for (int i = 0; i < m; i++) mx = fmax(mx, fabs((double)A[i * ld + i].re));
     dmax = mx;
   }
   __syncthreads();
@@ -45,8 +47,8 @@ __device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, double
     for (int r = 0; r < m - 1; r++) {
       for (int k = tid; k < np; k += nt) {
         const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
-        const T a = A[p * m + p].re, d = A[q * m + q].re;
-        const Cx<T> b = A[p * m + q];
+        const T a = A[p * ld + p].re, d = A[q * ld + q].re;
+        const Cx<T> b = A[p * ld + q];
         const T ab = sqrt(b.re * b.re + b.im * b.im);
         if (!(ab > SmallPrec<T>::eps * sqrt(fabs(a * d)) && ab > floor_abs && ab > (T)1e-300)) {
           rc[k] = 1; rs[k] = 0; re[k] = cx<T>(1, 0);
@@ -67,12 +69,12 @@ __device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, double
         const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
         const T c = rc[k], s = rs[k];
         const Cx<T> ph = re[k];
-        const Cx<T> ap = A[i * m + p], aq = ph * A[i * m + q];
-        A[i * m + p] = c * ap - s * aq;
-        A[i * m + q] = s * ap + c * aq;
-        const Cx<T> vp = V[i * m + p], vq = ph * V[i * m + q];
-        V[i * m + p] = c * vp - s * vq;
-        V[i * m + q] = s * vp + c * vq;
+        const Cx<T> ap = A[i * ld + p], aq = ph * A[i * ld + q];
+        A[i * ld + p] = c * ap - s * aq;
+        A[i * ld + q] = s * ap + c * aq;
+        const Cx<T> vp = V[i * ld + p], vq = ph * V[i * ld + q];
+        V[i * ld + p] = c * vp - s * vq;
+        V[i * ld + q] = s * vp + c * vq;
       }
       __syncthreads();
       for (int e = tid; e < np * m; e += nt) {        // A <- J^dag A (rows p, q)
@@ -81,9 +83,9 @@ __device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, T* rc, T* rs, Cx<T>* re, double
         const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
         const T c = rc[k], s = rs[k];
         const Cx<T> ph = conj(re[k]);
-        const Cx<T> ap = A[p * m + j], aq = ph * A[q * m + j];
-        A[p * m + j] = c * ap - s * aq;
-        A[q * m + j] = s * ap + c * aq;
+        const Cx<T> ap = A[p * ld + j], aq = ph * A[q * ld + j];
+        A[p * ld + j] = c * ap - s * aq;
+        A[q * ld + j] = s * ap + c * aq;
       }
       __syncthreads();
     }
@@ -101,9 +103,11 @@ __global__ void __launch_bounds__(256) k_small_rr(const double2* Gall, const dou
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int t = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const size_t mm = (size_t)m * m;
+  const int ld = m + 1;                  // padded rows of the work matrices
+  const size_t ml = (size_t)m * ld;
   Cx<T>*S, *A, *Z;
-  if (use_smem) { S = (Cx<T>*)sm_raw; A = S + mm; Z = A + mm; }
-  else { S = gwork + 3 * mm * t; A = S + mm; Z = A + mm; }
+  if (use_smem) { S = (Cx<T>*)sm_raw; A = S + ml; Z = A + ml; }
+  else { S = gwork + 3 * ml * t; A = S + ml; Z = A + ml; }
   __shared__ T rc[128], rs[128];
   __shared__ Cx<T> re[128];
   __shared__ double red[512], lam[256];
@@ -112,60 +116,61 @@ __global__ void __launch_bounds__(256) k_small_rr(const double2* Gall, const dou
   const double2* H = Hall + mm * t;
   // 1) eigen-decomposition of the Gram matrix
   for (size_t e = tid; e < mm; e += nt) {
-    A[e] = cx<T>((T)G[e].x, (T)G[e].y);
-    S[e] = cx<T>((e / m) == (e % m) ? (T)1 : (T)0, 0);
+    const int i = e / m, j = e % m;
+    A[i * ld + j] = cx<T>((T)G[e].x, (T)G[e].y);
+    S[i * ld + j] = cx<T>(i == j ? (T)1 : (T)0, 0);
   }
   __syncthreads();
-  const int sw_g = jacobi<T>(A, S, m, rc, rs, re, red);
+  const int sw_g = jacobi<T>(A, S, m, ld, rc, rs, re, red);
   // 2) S <- Q diag(g)^-1/2, dropping directions with g <= drop_rel gmax
   if (tid == 0) {
     double gmax = 0;
-    for (int i = 0; i < m; i++) gmax = fmax(gmax, (double)A[i * m + i].re);
+    for (int i = 0; i < m; i++) gmax = fmax(gmax, (double)A[i * ld + i].re);
     red[0] = gmax;
   }
   __syncthreads();
   const double gmax = red[0];
   __syncthreads();
   for (int i = tid; i < m; i += nt) {
-    const double gi = A[i * m + i].re;
+    const double gi = A[i * ld + i].re;
     lam[i] = gi > drop_rel * gmax ? 1.0 / sqrt(gi) : 0.0;
   }
   __syncthreads();
-  for (size_t e = tid; e < mm; e += nt) S[e] = (T)lam[e % m] * S[e];
+  for (size_t e = tid; e < mm; e += nt) S[(e / m) * ld + e % m] = (T)lam[e % m] * S[(e / m) * ld + e % m];
   __syncthreads();
   // 3) Z <- H S ; A <- S^dag Z  (= S^dag H S)
   for (size_t e = tid; e < mm; e += nt) {
     const int i = e / m, j = e % m;
     Cx<T> s = cx<T>(0, 0);
-    for (int l = 0; l < m; l++) fma_acc(s, cx<T>((T)H[i * m + l].x, (T)H[i * m + l].y), S[l * m + j]);
-    Z[e] = s;
+    for (int l = 0; l < m; l++) fma_acc(s, cx<T>((T)H[i * m + l].x, (T)H[i * m + l].y), S[l * ld + j]);
+    Z[i * ld + j] = s;
   }
   __syncthreads();
   for (size_t e = tid; e < mm; e += nt) {
     const int i = e / m, j = e % m;
     Cx<T> s = cx<T>(0, 0);
-    for (int l = 0; l < m; l++) fma_conj_acc(s, S[l * m + i], Z[l * m + j]);
-    A[e] = s;
+    for (int l = 0; l < m; l++) fma_conj_acc(s, S[l * ld + i], Z[l * ld + j]);
+    A[i * ld + j] = s;
   }
   __syncthreads();
   for (size_t e = tid; e < mm; e += nt) {   // hermitian part (round-off)
     const int i = e / m, j = e % m;
     if (i < j) {
-      const Cx<T> a = A[i * m + j], b = A[j * m + i];
+      const Cx<T> a = A[i * ld + j], b = A[j * ld + i];
       const Cx<T> h = cx<T>((T)0.5 * (a.re + b.re), (T)0.5 * (a.im - b.im));
-      A[i * m + j] = h;
-      A[j * m + i] = conj(h);
+      A[i * ld + j] = h;
+      A[j * ld + i] = conj(h);
     } else if (i == j) {
-      A[e].im = 0;
+      A[i * ld + j].im = 0;
     }
   }
-  for (size_t e = tid; e < mm; e += nt) Z[e] = cx<T>((e / m) == (e % m) ? (T)1 : (T)0, 0);
+  for (size_t e = tid; e < mm; e += nt) Z[(e / m) * ld + e % m] = cx<T>((e / m) == (e % m) ? (T)1 : (T)0, 0);
   __syncthreads();
-  const int sw_h = jacobi<T>(A, Z, m, rc, rs, re, red);
+  const int sw_h = jacobi<T>(A, Z, m, ld, rc, rs, re, red);
   if (tid == 0) { dropped[1 + 2 * t] = sw_g; dropped[2 + 2 * t] = sw_h; }
   // 4) sort ascending.  A dropped direction i has an exactly zero row and column
   //    in S^dag H S, so Jacobi never rotates it and it keeps position i: sort it last.
-  for (int i = tid; i < m; i += nt) lam[i] = lam[i] > 0 ? (double)A[i * m + i].re : 1e300;
+  for (int i = tid; i < m; i += nt) lam[i] = lam[i] > 0 ? (double)A[i * ld + i].re : 1e300;
   __syncthreads();
   for (int i = tid; i < m; i += nt) {
     int rank = 0;
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(256) k_small_rr(const double2* Gall, const dou
     const int i = e / m, j = e % m;
     const int zj = order[j];
     Cx<T> s = cx<T>(0, 0);
-    for (int l = 0; l < m; l++) fma_acc(s, S[i * m + l], Z[l * m + zj]);
+    for (int l = 0; l < m; l++) fma_acc(s, S[i * ld + l], Z[l * ld + zj]);
     Cout[e] = make_double2((double)s.re, (double)s.im);
   }
   for (int j = tid; j < m; j += nt) {
