@@ -268,20 +268,20 @@ __global__ void __launch_bounds__(256) k_resid(const Cx<R>* __restrict__ X, cons
                                                Cx<float>* Rout) {
   const int t = blockIdx.y;
   const int j = blockIdx.x * 32 + (threadIdx.x & 31), lane = threadIdx.x >> 5;
-  double s = 0;
+  R s = 0;   // in the block's precision (FP64 arithmetic is scarce next to an FP32 block)
   if (j < m) {
-    const double th = theta[(size_t)t * m + j];
+    const R th = (R)theta[(size_t)t * m + j];
     const size_t base = (size_t)t * n * m;
     for (int k = lane; k < n; k += 8) {
       const size_t idx = base + (size_t)k * m + j;
       const Cx<R> w = W[idx], x = X[idx];
-      const double dx = (double)w.re - th * (double)x.re, dy = (double)w.im - th * (double)x.im;
+      const R dx = w.re - th * x.re, dy = w.im - th * x.im;
       s += dx * dx + dy * dy;
       if (Rout) Rout[idx] = cx<float>((float)dx, (float)dy);
     }
   }
   __shared__ double red[8][33];
-  red[lane][threadIdx.x & 31] = s;
+  red[lane][threadIdx.x & 31] = (double)s;
   __syncthreads();
   if (lane == 0 && j < m) {
     double tot = 0;
