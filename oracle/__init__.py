@@ -21,6 +21,8 @@ Modules
   laplacian  the spatial covariant Laplacian of Eq. 1 and its low modes.
   dlma       distillation sources, projector, perambulator and the
              C_rest / C_mixed / C_dist contractions of Eqs. 2-4.
+  dilution   colour x even-odd diluted wall sources with spin-explicit
+             one-end insertion (Sec. 3) and the trace form they estimate.
 
 Parity status: every function is pinned by a test against a closed form, an
 invariant, brute force or a library routine, except the paper-level physics

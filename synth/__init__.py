@@ -144,6 +144,16 @@ def z2z2_noise(n: int, vol_s: int, seed: int) -> np.ndarray:
     return (sgn[..., 0] + 1j * sgn[..., 1]) / np.sqrt(2.0)
 
 
+def wall_noise(n: int, vol_s: int, seed: int) -> np.ndarray:
+    """n Z2 x Z2 wall-noise vectors on one timeslice: one number per site and
+    colour (no spin index) from {(+-1 +- i)/sqrt 2}, two independent bits each.
+    Returns complex128 [n, vol_s, 3]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    bits = rng.integers(0, 2, size=(n, vol_s, 3, 2))
+    sgn = 1.0 - 2.0 * bits.astype(np.float64)
+    return (sgn[..., 0] + 1j * sgn[..., 1]) / np.sqrt(2.0)
+
+
 def gaussian_spinors(n: int, V: int, seed: int) -> np.ndarray:
     """n complex Gaussian spinor fields [n, V, 4, 3] (test vectors)."""
     rng = np.random.Generator(np.random.PCG64(seed))
