@@ -239,6 +239,27 @@ dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_noise, const
                              double tol, dlma_prec inner, double* C_dist, double* C_rest,
                              double* C_mixed, dlma_solve_info* info, dlma_mem mem);
 
+/* dlma_correlators_diluted: the same pipeline with the noise treatment of the
+ * paper's measurements (Sec. 3: six colour and even-odd diluted wall sources
+ * per noise vector, solved for each of the four source spins -- the 24 wall
+ * sources of Fig. 1).  eta complex [n_noise][L^3][3] in `mem`: one Z2 x Z2
+ * number per site and colour of t_src, no spin index.  Piece d = 2 c + p keeps
+ * colour c on the sites of t_src with (x + y + z + t_src) mod 2 = p; every
+ * piece eta_d is solved as eta_d (x) e_beta and (1 - Box(t_src)) eta_d (x) e_beta
+ * (48 solves per noise vector), and with B = G g5 on the source spin
+ *   C_P(t) = 1/N_r sum_{r,d} sum_{beta,beta'} B[beta][beta'] sum_{x in t}
+ *            phibar_{d,beta'}^dag g5 G P_t phi_{d,beta},
+ * P_t = 1 - Box(t) (C_rest) or Box(t) (C_mixed): Eq. 3 with eta eta^dag
+ * replaced by sum_d eta_d eta_d^dag.  C_dist as in dlma_correlators.  Outputs
+ * complex [4][T] HOST (channels PS, V1, V2, V3); info (may be NULL) gets
+ * 4N + 48 n_noise records: the 4N distillation solves, then for noise r, piece
+ * d, the rows 4N + 48 r + 8 d + beta (phi) and + 4 + beta (phibar).  Solves run
+ * in batches of whole noise vectors within the memory cap.  Errors: STATE (no
+ * cached modes for N), INVALID_ARG (n_noise < 1), plus those of dlma_solve. */
+dlma_status dlma_correlators_diluted(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* eta,
+                                     double tol, dlma_prec inner, double* C_dist, double* C_rest,
+                                     double* C_mixed, dlma_solve_info* info, dlma_mem mem);
+
 /* dlma_set_checkpoint: on != 0 makes dlma_correlators keep its forward
  * solutions (the 4N distillation solutions and phi_r, phibar_r of every noise
  * vector; the Krylov iterates are never kept) for dlma_correlators_backward;

@@ -52,6 +52,7 @@ SIGNATURES = {
     "dlma_project": (_ST, [_P, _I, _P, _I, _P, _I, _P, _I]),
     "dlma_contract": (_ST, [_P, _I, _I, _P, _I, _P, _P, _P, _P, _I]),
     "dlma_correlators": (_ST, [_P, _I, _I, _I, _P, _D, _I, _P, _P, _P, _P, _I]),
+    "dlma_correlators_diluted": (_ST, [_P, _I, _I, _I, _P, _D, _I, _P, _P, _P, _P, _I]),
     "dlma_solve_adjoint": (_ST, [_P, _P, _P, _I, _D, _I, _P, _I]),
     "dlma_real_dot": (_ST, [_P, _P, _P, C.c_uint64, _P, _I]),
     "dlma_set_checkpoint": (_ST, [_P, _I]),

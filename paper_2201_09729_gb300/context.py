@@ -237,6 +237,20 @@ class Context:
                             converged=bool(i.converged)) for i in info]
         return res
 
+    def dlma_correlators_diluted(self, t_src: int, N: int, eta, tol: float, inner: int = L.FP32):
+        """Colour x even-odd diluted wall sources, spin-explicit; eta complex [n_noise, L^3, 3]."""
+        nn = eta.shape[0]
+        _check_c128(eta, (nn, self.Vs, 3), "eta")
+        out = [np.empty((4, self.T), dtype=np.complex128) for _ in range(3)]
+        info = (L.SolveInfo * (4 * N + 48 * nn))()
+        self._check(self.lib.dlma_correlators_diluted(self.h, int(t_src), int(N), nn, _ptr(eta), float(tol), inner,
+                                                      _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), info, _mem(eta)))
+        res = {"C_dist": out[0], "C_rest": out[1], "C_mixed": out[2]}
+        res["C"] = res["C_rest"] + 2 * res["C_mixed"] + res["C_dist"]
+        res["info"] = [dict(iters_inner=i.iters_inner, iters_outer=i.iters_outer, true_resid=i.true_resid,
+                            converged=bool(i.converged)) for i in info]
+        return res
+
     def dlma_index_tables(self):
         eo = np.empty(self.V, dtype=np.int32)
         nbr = np.empty((2, 8, self.V // 2), dtype=np.int32)

@@ -310,6 +310,90 @@ __global__ void __launch_bounds__(128) k_noise_parts(const double2* __restrict__
   }
 }
 
+// ---- colour x even-odd diluted wall sources, spin-explicit (Sec. 3) --------
+// Piece d = 2 c + p of noise r keeps colour c and the sites of t' with
+// (x + y + z + t') mod 2 = p.  Rows of the solution set after the 4N
+// distillation rows: 4N + 48 r + 8 d + 4 kind + beta, kind 0: phi_{d,beta} =
+// D^-1 (eta_d (x) e_beta), kind 1: phibar_{d,beta} = D^-1 ((1 - Box(t')) eta_d (x) e_beta).
+
+// H[r * 6 + d][m][spin 0][c] = eta_d(m, c) (other spins zero): the pieces as
+// spinor fields, so that the (1 - Box(t')) of the undiluted path applies unchanged
+__global__ void k_dilute(const double2* __restrict__ eta, int nn, int L, int t_src, double2* H) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int Vs = L * L * L;
+  if (e >= (size_t)nn * 6 * Vs) return;
+  const int m = (int)(e % Vs);
+  const int rd = (int)(e / Vs), r = rd / 6, d = rd % 6, c = d / 2, p = d % 2;
+  const int x = m % L, y = (m / L) % L, z = m / (L * L);
+  double2* out = H + e * 12;
+#pragma unroll
+  for (int q = 0; q < 12; q++) out[q] = make_double2(0, 0);
+  if ((x + y + z + t_src) % 2 == p) out[c] = eta[((size_t)r * Vs + m) * 3 + c];
+}
+
+// noise rows j in [j0, j0 + nb) (all >= 4N): b zeroed beforehand, timeslice t_src written
+__global__ void k_sources_dil(int j0, int nb, int N, int Vs, int t_src, const double2* __restrict__ H,
+                              const double2* __restrict__ pe, double2* b, size_t stride_sites) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)nb * Vs) return;
+  const int m = (int)(e % Vs), jl = (int)(e / Vs);
+  const int q = j0 + jl - 4 * N, r = q / 48, w = q % 48, d = w / 8, kind = (w % 8) / 4, beta = w % 4;
+  const double2* src = (kind == 0 ? H : pe) + ((size_t)(r * 6 + d) * Vs + m) * 12;   // spin 0 of the piece
+  double2* out = b + ((size_t)jl * stride_sites + (size_t)t_src * Vs + m) * 12;
+#pragma unroll
+  for (int c = 0; c < 3; c++) out[beta * 3 + c] = src[c];
+}
+
+// rest / mixed [ch][t] of the diluted estimator:
+//   1/N_r sum_{r,d,beta,beta'} B[beta][beta'] sum_{a,b} A[a][b] (W - Wbox)[beta' a][beta b]
+// W from the spin inner products M[(r, d, beta', beta)][t][a b], Wbox from the coefficients
+__global__ void __launch_bounds__(128) k_noise_parts_dil(const double2* __restrict__ M,
+                                                         const double2* __restrict__ coeff, int N, int T, int nn,
+                                                         int row0, SpinMats S, double2* rest, double2* mixed) {
+  const int t = blockIdx.x, ch = blockIdx.y;
+  Cx<double> mix = cx<double>(0, 0), full = cx<double>(0, 0);
+  const int per = 6 * 16 * N;                    // (d, beta', beta, k) per noise vector
+  for (int e = threadIdx.x; e < nn * per; e += blockDim.x) {
+    const int r = e / per, w = e % per;
+    const int d = w / (16 * N), bq = (w / N) % 16, k = w % N;
+    const int bp = bq / 4, bt = bq % 4;          // beta' (phibar), beta (phi)
+    const Cx<double> Bv = cx<double>(S.re[4 + ch][bt][bp], S.im[4 + ch][bt][bp]);
+    if (Bv.re == 0.0 && Bv.im == 0.0) continue;
+    const int rphi = row0 + 48 * r + 8 * d + bt, rbar = row0 + 48 * r + 8 * d + 4 + bp;
+    Cx<double> sm = cx<double>(0, 0), sf = cx<double>(0, 0);
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; b < 4; b++) {
+        const Cx<double> A = cx<double>(S.re[ch][a][b], S.im[ch][a][b]);
+        if (A.re == 0.0 && A.im == 0.0) continue;
+        const double2 ca = coeff[(((size_t)rbar * T + t) * 4 + a) * N + k];
+        const double2 cb = coeff[(((size_t)rphi * T + t) * 4 + b) * N + k];
+        fma_acc(sm, A, conj(cx<double>(ca.x, ca.y)) * cx<double>(cb.x, cb.y));
+        if (k == 0) {
+          const double2 mv = M[((((size_t)r * 6 + d) * 16 + bq) * T + t) * 16 + a * 4 + b];
+          fma_acc(sf, A, cx<double>(mv.x, mv.y));
+        }
+      }
+    fma_acc(mix, Bv, sm);
+    fma_acc(full, Bv, sf);
+  }
+  __shared__ double red[4][128];
+  red[0][threadIdx.x] = mix.re;
+  red[1][threadIdx.x] = mix.im;
+  red[2][threadIdx.x] = full.re;
+  red[3][threadIdx.x] = full.im;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 4; q++) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double inv = 1.0 / nn;
+    mixed[(size_t)ch * T + t] = make_double2(red[0][0] * inv, red[1][0] * inv);
+    rest[(size_t)ch * T + t] = make_double2((red[2][0] - red[0][0]) * inv, (red[3][0] - red[1][0]) * inv);
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -592,6 +676,119 @@ extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_n
   TRY(finish_contract(ctx, N, n_noise, coeff, M, C_dist, C_rest, C_mixed));
   CU(cudaEventRecord(e1, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  ctx->timing[0] = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return worst;
+}
+
+// ---------------------------------------------------------------------------
+// diluted wall sources (Sec. 3): 4N distillation solves + 48 per noise vector
+extern "C" dlma_status dlma_correlators_diluted(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* eta,
+                                                double tol, dlma_prec inner, double* C_dist, double* C_rest,
+                                                double* C_mixed, dlma_solve_info* info, dlma_mem mem) {
+  if (!ctx) return DLMA_ERR_INVALID_ARG;
+  if (!ctx->have_gauge || !ctx->have_params) return set_err(ctx, DLMA_ERR_STATE, "gauge / params not set");
+  if (N < 1 || n_noise < 1 || !eta || t_src < 0 || t_src >= ctx->g.T || !(tol > 0) || !C_dist || !C_rest ||
+      !C_mixed)
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_correlators_diluted");
+  if (ctx->eig_N != N) return set_err(ctx, DLMA_ERR_STATE, "no cached Laplacian modes for N = %d", N);
+  for (int t = 0; t < ctx->g.T; t++)
+    if (!ctx->eig_have[t]) return set_err(ctx, DLMA_ERR_STATE, "Laplacian modes of timeslice %d not computed", t);
+  CU(cudaSetDevice(ctx->device));
+  const int T = ctx->g.T, Vs = ctx->g.Vs, L = ctx->g.L;
+  const size_t V = ctx->g.V;
+  const int nn = n_noise, J = 4 * N + 48 * nn;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, ctx->stream));
+  const double* deta;
+  TRY(copy_in(ctx, WS_T0, eta, (size_t)nn * Vs * 3 * 16, mem, &deta));
+  double2* H;
+  TRY(workT(ctx, WS_CON, (size_t)nn * 6 * Vs * 12, &H));
+  {
+    const size_t tot = (size_t)nn * 6 * Vs;
+    k_dilute<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>((const double2*)deta, nn, L, t_src, H);
+    CHECK_LAUNCH();
+  }
+  double2 *VT, *VTs;
+  TRY(transpose_V(ctx, (const double*)ctx->eig_V, 1, T, T, 0, N, &VT, WS_PROJ_PART));
+  TRY(transpose_V(ctx, (const double*)ctx->eig_V, 1, T, 1, t_src, N, &VTs, WS_PROJ_V));
+  double2* pe;
+  TRY(project_noise(ctx, VTs, N, (const double*)H, 6 * nn, &pe));
+  double2* coeff;
+  TRY(workT(ctx, WS_PROJ_C, (size_t)J * T * 4 * N, &coeff));
+  double2* M;
+  TRY(workT(ctx, WS_T1, (size_t)nn * 6 * 16 * T * 16, &M));
+  size_t per_rhs = V * 12 * 16 * 2 + field_bytes_per_rhs(DLMA_FP64, ctx->g.Vh) * 7 +
+                   field_bytes_per_rhs(DLMA_FP32, ctx->g.Vh) * 8;
+  size_t freeb = 0, totb = 0;
+  cudaMemGetInfo(&freeb, &totb);
+  size_t budget = ctx->memcap ? ctx->memcap : (size_t)(0.8 * (double)freeb);
+  int nb = (int)std::max<size_t>(48, std::min<size_t>((size_t)J, budget / per_rhs));
+  double *b, *x;
+  TRY(workT(ctx, WS_SRC, (size_t)nb * V * 24, &b));
+  TRY(workT(ctx, WS_SOL, (size_t)nb * V * 24, &x));
+  std::vector<int> hp;
+  dlma_status worst = DLMA_OK;
+  int j0 = 0;
+  while (j0 < J) {
+    int cnt;
+    if (j0 < 4 * N) {
+      cnt = std::min(nb, 4 * N - j0);
+      TRY(sources_range(ctx, j0, cnt, N, t_src, VTs, nullptr, nullptr, b));
+    } else {
+      cnt = std::min(std::max(48, (nb / 48) * 48), J - j0);
+      CU(cudaMemsetAsync(b, 0, (size_t)cnt * V * 12 * 16, ctx->stream));
+      const size_t tot = (size_t)cnt * Vs;
+      k_sources_dil<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(j0, cnt, N, Vs, t_src, H, pe,
+                                                                          (double2*)b, V);
+      CHECK_LAUNCH();
+    }
+    dlma_status st = solve_fields(ctx, b, x, cnt, tol, inner, info ? info + j0 : nullptr);
+    if (st != DLMA_OK && st != DLMA_ERR_NOT_CONVERGED) return st;
+    if (st != DLMA_OK) worst = st;
+    TRY(project(ctx, VT, N, T, x, V, 0, cnt, coeff + (size_t)j0 * T * 4 * N));
+    if (j0 >= 4 * N) {
+      // spin inner products <phibar_{d,beta'}, phi_{d,beta}>_t of every piece in the batch
+      const int r0 = (j0 - 4 * N) / 48, nr = cnt / 48;
+      hp.assign((size_t)nr * 6 * 16 * 2, 0);
+      for (int r = 0; r < nr; r++)
+        for (int d = 0; d < 6; d++)
+          for (int bq = 0; bq < 16; bq++) {
+            const size_t pi = ((size_t)r * 6 + d) * 16 + bq;
+            hp[2 * pi] = 48 * r + 8 * d + 4 + bq / 4;   // phibar_{d, beta'}
+            hp[2 * pi + 1] = 48 * r + 8 * d + bq % 4;   // phi_{d, beta}
+          }
+      int* dp;
+      TRY(workT(ctx, WS_T2, hp.size(), &dp));
+      CU(cudaMemcpyAsync(dp, hp.data(), sizeof(int) * hp.size(), cudaMemcpyHostToDevice, ctx->stream));
+      dim3 grid(T, nr * 6 * 16);
+      k_spin_inner<<<grid, 256, 0, ctx->stream>>>((const double2*)x, V, Vs, dp, M + (size_t)r0 * 6 * 16 * T * 16, T);
+      CHECK_LAUNCH();
+      CU(cudaStreamSynchronize(ctx->stream));     // hp is reused by the next batch
+    }
+    j0 += cnt;
+  }
+  {
+    double2* out;
+    TRY(workT(ctx, WS_CON2, (size_t)12 * T, &out));
+    SpinMats S = spin_mats();
+    k_cdist<<<dim3(T, 4), 256, 0, ctx->stream>>>(coeff, N, T, S, out);
+    CHECK_LAUNCH();
+    k_noise_parts_dil<<<dim3(T, 4), 128, 0, ctx->stream>>>(M, coeff, N, T, nn, 4 * N, S, out + 4 * T, out + 8 * T);
+    CHECK_LAUNCH();
+    std::vector<double2> h(12 * T);
+    CU(cudaMemcpyAsync(h.data(), out, sizeof(double2) * 12 * T, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaEventRecord(e1, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    memcpy(C_dist, h.data(), sizeof(double2) * 4 * T);
+    memcpy(C_rest, h.data() + 4 * T, sizeof(double2) * 4 * T);
+    memcpy(C_mixed, h.data() + 8 * T, sizeof(double2) * 4 * T);
+  }
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
   ctx->timing[0] = ms;
