@@ -592,7 +592,8 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   m += m & 1;
   if (m > E.n) m = E.n - (E.n & 1);
   if (m < N) return set_err(ctx, DLMA_ERR_INVALID_ARG, "N too large for the timeslice");
-  if (m > 254) return set_err(ctx, DLMA_ERR_INVALID_ARG, "N + buffer above the eigensolver's limit of 254");
+  if (m > kSmallMaxM - 2)
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "N + buffer above the eigensolver's limit of %d", kSmallMaxM - 2);
   E.m = m;
   E.degree = 40;            // largest filter degree (phase B); phase A stays below 20
   E.blk = (size_t)m * Tn * E.n;

@@ -19,6 +19,10 @@ template <class T> struct SmallPrec;
 template <> struct SmallPrec<float> { static constexpr float eps = 1e-6f; };
 template <> struct SmallPrec<double> { static constexpr double eps = 1e-15; };
 
+// largest block (columns per timeslice) the small problems take: m/2 rotation
+// pairs and m sort keys live in static shared memory
+constexpr int kSmallMaxM = 512;
+
 __device__ __forceinline__ int rr_pos(int idx, int r, int m) { return idx == 0 ? 0 : ((idx - 1 + r) % (m - 1)) + 1; }
 
 // Diagonalise the hermitian A [m][m] (row-major with leading dimension ld, in
@@ -108,10 +112,10 @@ __global__ void __launch_bounds__(256) k_small_rr(const double2* Gall, const dou
   Cx<T>*S, *A, *Z;
   if (use_smem) { S = (Cx<T>*)sm_raw; A = S + ml; Z = A + ml; }
   else { S = gwork + 3 * ml * t; A = S + ml; Z = A + ml; }
-  __shared__ T rc[128], rs[128];
-  __shared__ Cx<T> re[128];
-  __shared__ double red[512], lam[256];
-  __shared__ int order[256];
+  __shared__ T rc[kSmallMaxM / 2], rs[kSmallMaxM / 2];
+  __shared__ Cx<T> re[kSmallMaxM / 2];
+  __shared__ double red[512], lam[kSmallMaxM];
+  __shared__ int order[kSmallMaxM];
   const double2* G = Gall + mm * t;
   const double2* H = Hall + mm * t;
   // 1) eigen-decomposition of the Gram matrix

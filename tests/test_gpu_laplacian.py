@@ -86,3 +86,23 @@ def test_eigs_precision_workload_sampled(dl):
         for k in (0, wl.n_modes // 2, wl.n_modes - 1):
             r = -lap.lap_apply(Ut, wl.L, V[t, k]) - lam[t, k] * V[t, k]
             assert np.linalg.norm(r) <= 1e-10 * max(1.0, lam[t, k])
+
+
+def test_eigs_block_above_256_columns(dl):
+    # N = 200 modes: a block of m = 264 columns per timeslice (past 256 rotation pairs
+    # of the former limit), checked against the dense spectrum and by residuals
+    L, T, N = 8, 2, 200
+    U = synth.gauge_field(L, T, 0.2, 231)
+    ctx = dl.Context(L, T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    lam, V = ctx.dlma_laplacian_eigs(-1, N, 1e-10)
+    for t in range(T):
+        Ut = lap.timeslice_links(U, L, t)
+        w, _ = lap.lap_modes(Ut, L, N + 1)
+        assert w[N] - w[N - 1] > 1e-6
+        assert np.all(np.abs(lam[t] - w[:N]) <= 1e-9 * np.maximum(np.abs(w[:N]), 1.0))
+        for k in (0, N // 2, N - 1):
+            r = -lap.lap_apply(Ut, L, V[t, k]) - lam[t, k] * V[t, k]
+            assert np.linalg.norm(r) <= 1e-9 * max(1.0, lam[t, k])
+        gram = np.einsum("kmc,lmc->kl", np.conj(V[t]), V[t])
+        assert np.abs(gram - np.eye(N)).max() < 1e-11
