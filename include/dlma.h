@@ -186,8 +186,12 @@ dlma_status dlma_apply_laplacian(dlma_ctx* ctx, const double* in, double* out, i
  * ([N], or [T][N] for t = -1; always HOST memory); eigenvectors, normalised,
  * go to evecs (complex [N][L^3][3], or [T][N][L^3][3]) in `mem`; evecs may be
  * NULL.  The modes of every computed timeslice are also cached in the
- * context.  Each pair meets ||lap v - lam v|| <= tol * max(|lam|, 1).
- * Errors: STATE, INVALID_ARG (N < 1 or N > 3 L^3 / 2), NOT_CONVERGED, CUDA. */
+ * context.  Each pair meets ||lap v - lam v|| <= tol * max(|lam|, 1).  The
+ * iteration keeps N + min(max(N, 16), 64) vectors per timeslice, at most 510.
+ * Below about 1e-10 the FP32 part of the iteration can stall a few times
+ * above tol, which is reported as NOT_CONVERGED with the residual reached.
+ * Errors: STATE, INVALID_ARG (N < 1, N > 3 L^3 / 2, or the block above 510
+ * vectors or 2^31 entries), NOT_CONVERGED, CUDA. */
 dlma_status dlma_laplacian_eigs(dlma_ctx* ctx, int t, int N, double tol, double* evals,
                                 double* evecs, dlma_mem mem);
 
