@@ -4,8 +4,8 @@
 One step = one pass of the whole hot path on the 16^3 x 32 precision workload
 (eps 0.2, kappa 0.1225, c_sw 1.0): the N = 32 lowest Laplacian modes of every
 timeslice, the 4N + 5 N_r = 168 sources of t' = 0 (N_r = 8 Z2 x Z2 noise
-vectors), their Wilson-clover solves to true residual 1e-10 (FP32 inner CGNE
-in FP64 defect correction, all right-hand sides batched), the V^dag psi
+vectors), their Wilson-clover solves to true residual 1e-10 (FP32 CGNE with
+FP64 reliable updates, all right-hand sides batched), the V^dag psi
 projections and the C_rest / C_mixed / C_dist contractions.
 
 value    = solves reaching 1e-10 per second of step time, all ranks (replicas)

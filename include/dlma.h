@@ -151,8 +151,11 @@ dlma_status dlma_apply_schur_noalloc(dlma_ctx* ctx, const double* in, double* ou
  * [nrhs][V][4][3]); the propagator solves of Eq. 4 and of the perambulator
  * (text after Eq. 3).  Even-odd Schur system, multi-RHS CG on the normal
  * equations; `inner` = DLMA_FP64 runs it in double precision, DLMA_FP32 /
- * DLMA_FP16S run the Krylov bulk in that precision inside FP64 defect
- * correction.  Each right-hand side stops when its FP64 true residual
+ * DLMA_FP16S run the Krylov iteration in that precision (FP16: storage, FP32
+ * arithmetic) with FP64 reliable updates: when a right-hand side's iterated
+ * residual has dropped by a fixed factor since its last update, its solution
+ * is folded into FP64 and its residual recomputed in FP64.  Each right-hand
+ * side stops when its FP64 true residual
  * ||b - D x|| / ||b|| <= tol and is retired from the batch.  `info` (may be
  * NULL) receives nrhs records.  A zero source gives x = 0.
  * Errors: STATE, INVALID_ARG (tol <= 0, nrhs < 1), NOT_CONVERGED, NONFINITE,
