@@ -18,8 +18,10 @@
 // in FP32, on the residual: with R = A X - X Theta and the filter's scalar
 // recurrence s_k(theta), p_k(A) X = X s_k(Theta) + E_k where
 //   E_{k+1} = a_k A E_k + b_k E_k + c_k E_{k-1} + a_k R s_k(Theta),  E_0 = 0,
-// so the FP32 rounding only touches the (small) E, and Y = X s_d + E_d is formed
-// in FP64.  Stops when every wanted pair has ||A x - theta x|| <= tol max(theta, 1).
+// so the FP32 rounding only touches the (small) E, and Y = X + E_d / s_d (the
+// filtered block with every column divided by its own s_d, so that the Gram
+// matrix stays well conditioned) is formed in FP64.  Stops when every wanted
+// pair has ||A x - theta x|| <= tol max(theta, 1).
 //
 // Block layout (row-major per timeslice): element (t, row r = 3 site + colour,
 // column j) of a batch of Tn timeslices at (t * 3 Vs + r) * m + j, so a warp
@@ -290,7 +292,11 @@ __global__ void __launch_bounds__(256) k_resid(const Cx<R>* __restrict__ X, cons
   }
 }
 
-// Y64 = X64 s[t][j] + E32  (phase B filter output)
+// Y64 = X64 + E32 / s[t][j]  (phase B filter output, column j divided by s_d(theta_j)).
+// The division leaves the span, and so the Rayleigh-Ritz, unchanged, but keeps the
+// columns of Y at unit scale: X s_d + E has columns from 1 down to 1 / rho, whose
+// Gram matrix (condition number up to rho^2) would limit the FP64 Ritz vectors
+// near the cut to a few 1e-10.  s_d(theta) >= 1 / rho > 0 on [theta_0, cut].
 __global__ void k_combine(const Cx<double>* __restrict__ X, const Cx<float>* __restrict__ E,
                           const double* __restrict__ scol, size_t nm, int m, size_t total, Cx<double>* Y) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -298,9 +304,9 @@ __global__ void k_combine(const Cx<double>* __restrict__ X, const Cx<float>* __r
   const unsigned e32 = (unsigned)e;           // total < 2^31 (checked with the block)
   const int j = (int)(e32 % (unsigned)m);
   const unsigned t = e32 / (unsigned)nm;
-  const double s = scol[t * m + j];
+  const double inv = 1.0 / scol[t * m + j];
   const Cx<float> ev = E[e];
-  Y[e] = s * X[e] + cx<double>((double)ev.re, (double)ev.im);
+  Y[e] = X[e] + inv * cx<double>((double)ev.re, (double)ev.im);
 }
 
 template <class A, class B> __global__ void k_convert_block(const Cx<A>* in, Cx<B>* out, size_t total) {
@@ -718,7 +724,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
       ec = en;
       en = t;
     }
-    // Y = X s_d + E_d
+    // Y = (X s_d + E_d) / s_d column by column
     k_combine<<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X64, ec, E.scol + (size_t)dB * Tn * m,
                                                                         (size_t)E.n * m, m, E.blk, Y64);
     CHECK_LAUNCH();

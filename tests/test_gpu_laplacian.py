@@ -106,3 +106,18 @@ def test_eigs_block_above_256_columns(dl):
             assert np.linalg.norm(r) <= 1e-9 * max(1.0, lam[t, k])
         gram = np.einsum("kmc,lmc->kl", np.conj(V[t]), V[t])
         assert np.abs(gram - np.eye(N)).max() < 1e-11
+
+
+def test_eigs_tight_tolerance_small_lattice(dl):
+    # 6^3 x 4 with N = 4 to 1e-12: the filtered columns of the FP64 phase are
+    # rescaled to unit size, so the Gram matrix does not limit the accuracy
+    L, T, N = 6, 4, 4
+    U = synth.gauge_field(L, T, 0.2, 405)
+    ctx = dl.Context(L, T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    lam, V = ctx.dlma_laplacian_eigs(-1, N, 1e-12)
+    for t in range(T):
+        Ut = lap.timeslice_links(U, L, t)
+        for k in range(N):
+            r = -lap.lap_apply(Ut, L, V[t, k]) - lam[t, k] * V[t, k]
+            assert np.linalg.norm(r) <= 1e-12 * max(1.0, lam[t, k])
