@@ -191,8 +191,8 @@ dlma_status dlma_apply_laplacian(dlma_ctx* ctx, const double* in, double* out, i
  * NULL.  The modes of every computed timeslice are also cached in the
  * context.  Each pair meets ||lap v - lam v|| <= tol * max(|lam|, 1).  The
  * iteration keeps N + min(max(N, 16), 64) vectors per timeslice, at most 510.
- * Below about 1e-10 the FP32 part of the iteration can stall a few times
- * above tol, which is reported as NOT_CONVERGED with the residual reached.
+ * An iteration that stops improving before tol returns NOT_CONVERGED with
+ * the residual reached.
  * Errors: STATE, INVALID_ARG (N < 1, N > 3 L^3 / 2, or the block above 510
  * vectors or 2^31 entries), NOT_CONVERGED, CUDA. */
 dlma_status dlma_laplacian_eigs(dlma_ctx* ctx, int t, int N, double tol, double* evals,
