@@ -39,8 +39,25 @@ PROFILE = os.path.join(ROOT, "profiles", "hop_fp32_precision_16c32.json")
 FALLBACK_HBM_GBS = 6800.0
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of a per-rank number over the process group (the slowest
+    replica sets the step time); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Units per second of the whole job: every replica processes units_per_rank
+    units per step of ms milliseconds (the max over ranks)."""
+    return units_per_rank * world / (ms / 1000.0)
+
+
 def _peaks():
-    for p in (os.path.join(ROOT, "MEASURED_PEAKS.json"), "/root/repo/MEASURED_PEAKS.json"):
+    for p in (os.path.join(ROOT, "MEASURED_PEAKS.json"),):
         if os.path.exists(p):
             try:
                 d = json.load(open(p))
@@ -274,13 +291,10 @@ def main():
     torch.cuda.synchronize()
     launches = ctx.dlma_kernel_launches() - l0
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, f"cuda:{local}")
     if dist:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = J * world / (ms / 1000.0)
+    value = whole_job_rate(J, world, ms)
     iters = [i["iters_inner"] for i in res["info"]]
 
     # e2e: the same step through HOST buffers, links / noise in, correlators out
@@ -298,7 +312,7 @@ def main():
             r2 = ctx.dlma_correlators(tp, N, eta_np[i], wl.tol, inner)
             ok = ok and all(x["converged"] for x in r2["info"])
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0 / args.steps, dist, f"cuda:{local}")
     h2d = U_np.nbytes + sum(e.nbytes for e in eta_np)
     d2h = 3 * r2["C_dist"].nbytes * len(wl.t_src) + 8 * wl.T * N
     assert ok
@@ -347,7 +361,7 @@ def main():
                                f"reliable updates",
                    "solves_per_step": J, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per-step working set > 10 GB)"},
-        "e2e": {"value": J * world / (e2e_ms / 1000.0), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": whole_job_rate(J, world, e2e_ms), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches // args.steps),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
