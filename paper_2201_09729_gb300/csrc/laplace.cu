@@ -304,9 +304,12 @@ __global__ void k_combine(const Cx<double>* __restrict__ X, const Cx<float>* __r
   const unsigned e32 = (unsigned)e;           // total < 2^31 (checked with the block)
   const int j = (int)(e32 % (unsigned)m);
   const unsigned t = e32 / (unsigned)nm;
-  const double inv = 1.0 / scol[t * m + j];
+  const double sj = scol[t * m + j];
   const Cx<float> ev = E[e];
-  Y[e] = X[e] + inv * cx<double>((double)ev.re, (double)ev.im);
+  const Cx<double> ed = cx<double>((double)ev.re, (double)ev.im);
+  // a vanishing s_d (possible only when the cut is pushed below 12 on a block that
+  // spans nearly the whole timeslice) keeps the unscaled column
+  Y[e] = fabs(sj) > 1e-280 ? X[e] + (1.0 / sj) * ed : sj * X[e] + ed;
 }
 
 template <class A, class B> __global__ void k_convert_block(const Cx<A>* in, Cx<B>* out, size_t total) {
