@@ -138,11 +138,13 @@ dlma_status dlma_apply_schur(dlma_ctx* ctx, const double* in, double* out, int n
  * no counterpart; it is a library-usage variant.  `in` and `out` are DEVICE
  * pointers (complex [nrhs][V/2][4][3], even sites), owned by the caller.  The
  * work space is a fixed 64 MiB array in the library's device memory, held by
- * every GPU that loads the library until the process exits; nothing else is
- * allocated.  Three FP64 even-odd fields of nrhs right-hand sides must fit in
- * it (3 * 192 * nrhs * V/2 bytes <= 64 MiB), else DLMA_ERR_INVALID_ARG with a
- * message.  The first call on a device looks up the array's device address;
- * make that first call before any stream capture.  All calls share the one
+ * every GPU that has loaded it until the process exits; nothing else is
+ * allocated.  The library's device code is loaded lazily (per device, on first
+ * use), so the 64 MiB are reserved on a device by the first call there, which
+ * also looks up the array's device address: make that first call before any
+ * stream capture.  Three FP64 even-odd fields of nrhs right-hand sides must
+ * fit in it (3 * 192 * nrhs * V/2 bytes <= 64 MiB), else DLMA_ERR_INVALID_ARG
+ * with a message.  All calls share the one
  * array: calls that overlap on the GPU race on it.
  * Errors: STATE, INVALID_ARG, CUDA. */
 dlma_status dlma_apply_schur_noalloc(dlma_ctx* ctx, const double* in, double* out, int nrhs, int dagger);
@@ -226,25 +228,36 @@ dlma_status dlma_project(dlma_ctx* ctx, int t, const double* V, int N, const dou
  * [4N + 5 n_noise][V][4][3], in that order) and the modes of every timeslice
  * (V complex [T][N][L^3][3]).  For the four channels G in (gamma_5, gamma_1,
  * gamma_2, gamma_3), with sink and source Gamma equal:
- *   C_dist(t)  = tr[g5 G tau(t) G g5 tau(t)^dag],  tau = V(t)^dag D^-1 V(t')
- *   C_mixed(t) = 1/N_r sum_r sum_{x in t} chi_r^dag g5 G Box(t) phi_r
- *   C_rest(t)  = 1/N_r sum_r sum_{x in t} chi_r^dag g5 G (1 - Box(t)) phi_r
+ *   C_dist(t)      = tr[g5 G tau(t) G g5 tau(t)^dag],  tau = V(t)^dag D^-1 V(t')
+ *   C_mixed(t)     = 1/N_r sum_r sum_{x in t} chi_r^dag g5 G Box(t) phi_r
+ *   C_rest(t)      = 1/N_r sum_r sum_{x in t} chi_r^dag g5 G (1 - Box(t)) phi_r
+ *   C_mixed_src(t) = tr[g5 G (1 - Box(t)) S G g5 Box(t') S^dag], S = D^-1(t, t'):
+ *                    the other mixed term of Eq. 2 (Box at the source, 1 - Box
+ *                    at the sink), exact and noise-free from the distillation
+ *                    solutions phi^(k,b):  sum_{k,b,b'} (G g5)_{b'b}
+ *                    <phi^(k,b), g5 G phi^(k,b')>_t - C_dist(t)
+ *   C_full(t)      = C_rest + 2 C_mixed + C_dist, the total of Eq. 2 (the two
+ *                    mixed terms merged by time reversal as the paper does;
+ *                    C_mixed - C_mixed_src measures what that merge neglects
+ *                    on one configuration)
  * chi_r = phibar_r (G = g5) or the gamma_5 gamma_k solution (G = g_k).
- * Outputs are complex [4][T] (channel-major), always HOST memory.
- * Errors: INVALID_ARG, CUDA. */
+ * Outputs are complex [4][T] (channel-major), always HOST memory; C_mixed_src
+ * and C_full may be NULL.  Errors: INVALID_ARG, CUDA. */
 dlma_status dlma_contract(dlma_ctx* ctx, int t_src, int N, const double* V, int n_noise,
                           const double* phi, double* C_dist, double* C_rest, double* C_mixed,
-                          dlma_mem mem);
+                          double* C_mixed_src, double* C_full, dlma_mem mem);
 
 /* dlma_correlators: the whole per-source-timeslice pipeline on the device --
  * sources, solves (precision `inner`, tolerance tol, in batches that fit the
  * memory cap), projections and contractions -- using the modes cached by
  * dlma_laplacian_eigs(t = -1, N).  eta complex [n_noise][L^3][4][3] in
- * `mem`; outputs complex [4][T] HOST; info (may be NULL) gets 4N + 5 n_noise
- * records.  Errors: STATE (no cached modes for N), plus those of dlma_solve. */
+ * `mem`; outputs complex [4][T] HOST as in dlma_contract (C_mixed_src and
+ * C_full may be NULL); info (may be NULL) gets 4N + 5 n_noise records.
+ * Errors: STATE (no cached modes for N), plus those of dlma_solve. */
 dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* eta,
                              double tol, dlma_prec inner, double* C_dist, double* C_rest,
-                             double* C_mixed, dlma_solve_info* info, dlma_mem mem);
+                             double* C_mixed, double* C_mixed_src, double* C_full,
+                             dlma_solve_info* info, dlma_mem mem);
 
 /* dlma_correlators_diluted: the same pipeline with the noise treatment of the
  * paper's measurements (Sec. 3: six colour and even-odd diluted wall sources
@@ -257,21 +270,51 @@ dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_noise, const
  *   C_P(t) = 1/N_r sum_{r,d} sum_{beta,beta'} B[beta][beta'] sum_{x in t}
  *            phibar_{d,beta'}^dag g5 G P_t phi_{d,beta},
  * P_t = 1 - Box(t) (C_rest) or Box(t) (C_mixed): Eq. 3 with eta eta^dag
- * replaced by sum_d eta_d eta_d^dag.  C_dist as in dlma_correlators.  Outputs
- * complex [4][T] HOST (channels PS, V1, V2, V3); info (may be NULL) gets
- * 4N + 48 n_noise records: the 4N distillation solves, then for noise r, piece
- * d, the rows 4N + 48 r + 8 d + beta (phi) and + 4 + beta (phibar).  Solves run
- * in batches of whole noise vectors within the memory cap.  Errors: STATE (no
- * cached modes for N), INVALID_ARG (n_noise < 1), plus those of dlma_solve. */
+ * replaced by sum_d eta_d eta_d^dag.  C_dist, C_mixed_src and C_full as in
+ * dlma_contract.  Outputs complex [4][T] HOST (channels PS, V1, V2, V3; the
+ * last two may be NULL); info (may be NULL) gets 4N + 48 n_noise records: the
+ * 4N distillation solves, then for noise r, piece d, the rows
+ * 4N + 48 r + 8 d + beta (phi) and + 4 + beta (phibar).  Solves run in batches
+ * of whole noise vectors within the memory cap.  Errors: STATE (no cached
+ * modes for N), INVALID_ARG (n_noise < 1), plus those of dlma_solve. */
 dlma_status dlma_correlators_diluted(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* eta,
                                      double tol, dlma_prec inner, double* C_dist, double* C_rest,
-                                     double* C_mixed, dlma_solve_info* info, dlma_mem mem);
+                                     double* C_mixed, double* C_mixed_src, double* C_full,
+                                     dlma_solve_info* info, dlma_mem mem);
+
+/* dlma_correlators_plain: the plain one-end stochastic estimator of the same
+ * correlator without distillation (no Box anywhere): the comparison the
+ * paper draws in Fig. 1.  diluted = 0: eta complex [n_noise][L^3][4][3]
+ * (undiluted Z2 x Z2 noise on t_src), 4 solves per noise vector, phi_r =
+ * D^-1 eta_r and chi_{r,k} = D^-1 g5 g_k eta_r, and
+ *   C(t) = 1/N_r sum_r sum_{x in t} chi_r^dag g5 G phi_r   (chi_r = phi_r for G = g5);
+ * info rows 4 r + q (q = 0: phi_r, q = k: chi_{r,k}).  diluted = 1: eta
+ * complex [n_noise][L^3][3] diluted as in dlma_correlators_diluted, 24 solves
+ * per noise vector (rows 24 r + 4 d + beta: phi_{d,beta}) and
+ *   C(t) = 1/N_r sum_{r,d} sum_{beta,beta'} (G g5)[beta][beta'] sum_{x in t}
+ *          phi_{d,beta'}^dag g5 G phi_{d,beta}.
+ * Needs no Laplacian modes.  C complex [4][T] HOST (channels PS, V1, V2, V3).
+ * Errors: STATE (no gauge / params), INVALID_ARG, plus those of dlma_solve. */
+dlma_status dlma_correlators_plain(dlma_ctx* ctx, int t_src, int n_noise, const double* eta, int diluted,
+                                   double tol, dlma_prec inner, double* C, dlma_solve_info* info,
+                                   dlma_mem mem);
 
 /* dlma_set_checkpoint: on != 0 makes dlma_correlators keep its forward
  * solutions (the 4N distillation solutions and phi_r, phibar_r of every noise
  * vector; the Krylov iterates are never kept) for dlma_correlators_backward;
- * on = 0 releases them. */
+ * on = 0 releases them.  The checkpoint holds (4N + 2 n_noise) V 192 bytes of
+ * device memory from the first checkpointed forward until it is released;
+ * while on, every dlma_correlators call also pays the device-to-device copies
+ * into it.  Each checkpointed forward overwrites the previous checkpoint and
+ * gets a new serial number (dlma_checkpoint_serial). */
 dlma_status dlma_set_checkpoint(dlma_ctx* ctx, int on);
+
+/* dlma_checkpoint_serial: serial number of the checkpoint currently held
+ * (1, 2, ... per checkpointed dlma_correlators call), 0 if none.  A caller
+ * that ran several forwards before their backwards compares it with the
+ * serial seen after its own forward and re-runs that forward if another one
+ * has replaced the checkpoint. */
+uint64_t dlma_checkpoint_serial(const dlma_ctx* ctx);
 
 /* dlma_correlators_backward: gradients of L = sum_t w(t) Re C_PS(t), C_PS the
  * pseudoscalar total C_rest + 2 C_mixed + C_dist of the last checkpointed
@@ -282,8 +325,11 @@ dlma_status dlma_set_checkpoint(dlma_ctx* ctx, int on);
  * (distillation), G(phi_r) = w/N_r (1 + Box) phibar_r, G(phibar_r) =
  * w/N_r (1 + Box) phi_r; then dL/dm0 = -sum_j Re <y_j, phi_j> and
  * dL/deta_r = y_{phi_r} + (1 - Box(t')) y_{phibar_r} on t'.  info (may be NULL)
- * gets 4N + 2 n_noise records.  Errors: STATE (no checkpoint / modes),
- * INVALID_ARG, plus those of dlma_solve. */
+ * gets 4N + 2 n_noise records.  The gradients belong to the state the
+ * checkpointed forward ran under: if m0, c_sw, the gauge field or the cached
+ * modes changed since, the call fails with STATE instead of differentiating
+ * the wrong operator.  Errors: STATE (no checkpoint / modes, or state changed
+ * since the checkpoint), INVALID_ARG, plus those of dlma_solve. */
 dlma_status dlma_correlators_backward(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* w,
                                       double tol, dlma_prec inner, double* dL_dm0, double* dL_deta,
                                       dlma_solve_info* info, dlma_mem mem);
@@ -300,10 +346,22 @@ dlma_status dlma_index_tables(dlma_ctx* ctx, int32_t* eo_index, int32_t* nbr);
  * context since creation (graph-replayed kernels included). */
 uint64_t dlma_kernel_launches(const dlma_ctx* ctx);
 
-/* dlma_last_timing_ms: device time (CUDA events on the context's stream) of
- * named phases of the last call: index 0 the whole call, 1 the dominant
- * stencil kernel summed, 2 the number of dominant-kernel launches. */
-dlma_status dlma_last_timing(const dlma_ctx* ctx, double* out3);
+/* dlma_last_timing: figures of the last timed call, measured with CUDA
+ * events on the context's stream (milliseconds unless stated); out[0 .. n-1]
+ * receives slots 0 .. n-1 (slots past 7 are 0).  Slot 0 is the device time of
+ * the whole call for every call below; the others depend on the call:
+ *   dlma_apply_schur          1 the two stencil launches, 2 their number (2)
+ *   dlma_solve, _adjoint      -
+ *   dlma_laplacian_eigs       1 FP32 filter iterations, 2 FP64 iterations,
+ *                             3 Laplacian applications (the matvec of Table 2),
+ *                             4 orthogonalisation: Gram matrices, small
+ *                               eigenproblems, rotations, residuals,
+ *                             5 host steps and transfers
+ *   dlma_correlators, _diluted, _plain
+ *                             1 source construction, 2 solves, 3 projections,
+ *                             4 contractions
+ * Errors: INVALID_ARG. */
+dlma_status dlma_last_timing(const dlma_ctx* ctx, double* out, int n);
 
 #ifdef __cplusplus
 }

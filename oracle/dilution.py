@@ -110,7 +110,41 @@ def diluted_correlators(solve, V_all, eta_wall, L, T, tp):
     phibar = solve(bb.reshape(Nr * 24, V, 4, 3)).reshape(Nr, 6, 4, V, 4, 3)
     rest, mixed = diluted_noise_parts(V_all, phi, phibar, L, T)
     return {"C_dist": cd, "C_rest": rest, "C_mixed": mixed, "C": rest + 2 * mixed + cd,
-            "phi": phi, "phibar": phibar}
+            "phi": phi, "phibar": phibar, "phi_dist": phid}
+
+
+def plain_diluted(phi, L, T):
+    """The plain (no distillation) estimator with spin-explicit diluted
+    sources: Eq. 3's trace with no Box, eta eta^dag -> sum_d eta_d eta_d^dag,
+        C(t) = 1/N_r sum_{r,d} sum_{beta,beta'} B[beta,beta'] sum_{x in t}
+               phi_{d,beta'}(x)^dag g5 G phi_{d,beta}(x),   B = G g5,
+    from phi [N_r, n_pieces, 4 (beta), V, 4, 3], phi_{d,beta} = D^-1 (eta_d (x) e_beta)
+    (any number of pieces per noise vector).  Returns complex [4, T]."""
+    Nr = phi.shape[0]
+    out = np.zeros((4, T), dtype=np.complex128)
+    for t in range(T):
+        ph = dlma.timeslice(phi, L, t)
+        for ch, G in enumerate(g.CHANNELS):
+            A = g.GAMMA5 @ G
+            B = G @ g.GAMMA5
+            Aph = np.einsum("st,rdbmtc->rdbmsc", A, ph)
+            W = np.einsum("rdqmsc,rdbmsc->rdqb", np.conj(ph), Aph)     # [r, d, beta', beta]
+            out[ch, t] = np.einsum("bq,rdqb->", B, W) / Nr
+    return out
+
+
+def plain_diluted_correlators(solve, eta_wall, L, T, tp):
+    """The plain estimator with the six colour x even-odd diluted wall sources
+    of every noise vector eta_wall [N_r, Vs, 3]: 24 solves per noise vector."""
+    Nr = eta_wall.shape[0]
+    V = L ** 3 * T
+    eta_d = dilution_pieces(eta_wall, L, tp)
+    sl = slice(tp * L ** 3, (tp + 1) * L ** 3)
+    b = np.zeros((Nr, 6, 4, V, 4, 3), dtype=np.complex128)
+    for beta in range(4):
+        b[:, :, beta, sl, beta, :] = eta_d
+    phi = solve(b.reshape(Nr * 24, V, 4, 3)).reshape(Nr, 6, 4, V, 4, 3)
+    return plain_diluted(phi, L, T), phi
 
 
 def source_outer(pieces):

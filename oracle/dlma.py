@@ -112,6 +112,60 @@ def noise_parts(V_all, phi, phibar, psibar, L, T):
     return rest, mixed
 
 
+def mixed_src(V_all, phi_dist, L, T):
+    """The source-side mixed term of Eq. 2 (Box at the source, 1 - Box at the
+    sink), exact, from the distillation solutions phi_dist [4 N_c, V, 4, 3]
+    (row 4k + beta solves v_k(t') (x) e_beta).  With Box(t') = sum_{k,beta}
+    w_{k beta} w_{k beta}^dag, w = v_k(t') (x) e_beta, and S w = phi:
+        tr[g5 G (1 - Box(t)) S G g5 Box(t') S^dag]
+          = sum_{k, b, b'} (G g5)_{b' b} <phi^(k,b), g5 G (1 - Box(t)) phi^(k,b')>_t.
+    Returns complex [4, T] over the channels (PS, V1, V2, V3)."""
+    Nc = phi_dist.shape[0] // 4
+    out = np.zeros((4, T), dtype=np.complex128)
+    for t in range(T):
+        ph = timeslice(phi_dist, L, t)
+        pr = (ph - box(V_all[t], ph)).reshape(Nc, 4, L ** 3, 4, 3)
+        ph = ph.reshape(Nc, 4, L ** 3, 4, 3)
+        for ch, G in enumerate(g.CHANNELS):
+            A = g.GAMMA5 @ G
+            B = G @ g.GAMMA5
+            Apr = np.einsum("st,kbmtc->kbmsc", A, pr)
+            # W[k, b, b'] = <phi^(k,b), A (1 - Box) phi^(k,b')>_t
+            W = np.einsum("kbmsc,kqmsc->kbq", np.conj(ph), Apr)
+            out[ch, t] = np.einsum("qb,kbq->", B, W)
+    return out
+
+
+def plain_sources(eta, L, T, tp):
+    """Sources of the plain (no distillation) one-end estimator with undiluted
+    noise eta [N_r, Vs, 4, 3] on t': [N_r, 4, V, 4, 3] = eta, g5 g_k eta (k = 1..3)."""
+    Nr, Vs = eta.shape[0], eta.shape[1]
+    b = np.zeros((Nr, 4, L ** 3 * T, 4, 3), dtype=np.complex128)
+    sl = slice(tp * Vs, (tp + 1) * Vs)
+    b[:, 0, sl] = eta
+    for k in range(1, 4):
+        b[:, k, sl] = np.einsum("st,rmtc->rmsc", g.GAMMA5 @ g.GAMMA[k], eta)
+    return b
+
+
+def plain_estimator(phi, chi, L, T):
+    """The plain stochastic estimator of the correlator of Eq. 2's left-hand
+    side (no Box anywhere): by cyclicity tr[g5 G S eta eta^dag G g5 S^dag] =
+    <S g5 G eta, g5 G S eta>, so with phi_r = D^-1 eta_r and
+    chi_{r,k} = D^-1 g5 g_k eta_r (chi = phi for G = g5)
+        C(t) = 1/N_r sum_r sum_{x in t} chi_r^dag g5 G phi_r.
+    phi [N_r, V, 4, 3], chi [N_r, 3, V, 4, 3].  Returns complex [4, T]."""
+    Nr = phi.shape[0]
+    out = np.zeros((4, T), dtype=np.complex128)
+    for t in range(T):
+        ph = timeslice(phi, L, t)
+        for ch, G in enumerate(g.CHANNELS):
+            left = ph if ch == 0 else timeslice(chi[:, ch - 1], L, t)
+            Aph = np.einsum("st,rmtc->rmsc", g.GAMMA5 @ G, ph)
+            out[ch, t] = np.vdot(left.ravel(), Aph.ravel()) / Nr
+    return out
+
+
 def dlma_correlators(solve, V_all, eta, L, T, tp):
     """The whole estimator of Eqs. 2-4 on one configuration.
 

@@ -50,16 +50,18 @@ SIGNATURES = {
     "dlma_laplacian_eigs": (_ST, [_P, _I, _I, _D, _P, _P, _I]),
     "dlma_make_sources": (_ST, [_P, _I, _I, _P, _I, _P, _P, _I]),
     "dlma_project": (_ST, [_P, _I, _P, _I, _P, _I, _P, _I]),
-    "dlma_contract": (_ST, [_P, _I, _I, _P, _I, _P, _P, _P, _P, _I]),
-    "dlma_correlators": (_ST, [_P, _I, _I, _I, _P, _D, _I, _P, _P, _P, _P, _I]),
-    "dlma_correlators_diluted": (_ST, [_P, _I, _I, _I, _P, _D, _I, _P, _P, _P, _P, _I]),
+    "dlma_contract": (_ST, [_P, _I, _I, _P, _I, _P, _P, _P, _P, _P, _P, _I]),
+    "dlma_correlators": (_ST, [_P, _I, _I, _I, _P, _D, _I, _P, _P, _P, _P, _P, _P, _I]),
+    "dlma_correlators_diluted": (_ST, [_P, _I, _I, _I, _P, _D, _I, _P, _P, _P, _P, _P, _P, _I]),
+    "dlma_correlators_plain": (_ST, [_P, _I, _I, _P, _I, _D, _I, _P, _P, _I]),
     "dlma_solve_adjoint": (_ST, [_P, _P, _P, _I, _D, _I, _P, _I]),
     "dlma_real_dot": (_ST, [_P, _P, _P, C.c_uint64, _P, _I]),
     "dlma_set_checkpoint": (_ST, [_P, _I]),
+    "dlma_checkpoint_serial": (C.c_uint64, [_P]),
     "dlma_correlators_backward": (_ST, [_P, _I, _I, _I, _P, _D, _I, _P, _P, _P, _I]),
     "dlma_index_tables": (_ST, [_P, _P, _P]),
     "dlma_kernel_launches": (C.c_uint64, [_P]),
-    "dlma_last_timing": (_ST, [_P, _P]),
+    "dlma_last_timing": (_ST, [_P, _P, _I]),
 }
 
 _lib = None

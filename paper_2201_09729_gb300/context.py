@@ -69,6 +69,7 @@ class Context:
                     stream = torch.cuda.current_stream(device).cuda_stream
             except Exception:
                 stream = None
+        self.params = None          # (m0, c_sw) last set on the context
         lat = L.Lattice(L_, T, bc_t)
         h = C.c_void_p()
         st = self.lib.dlma_create(C.byref(lat), device, C.c_void_p(stream) if stream else None, C.byref(h))
@@ -108,10 +109,12 @@ class Context:
 
     def dlma_set_gauge(self, U):
         _check_c128(U, (self.V, 4, 3, 3), "links")
+        self.params = None
         self._check(self.lib.dlma_set_gauge(self.h, _ptr(U), _mem(U)))
 
     def dlma_set_params(self, m0: float, c_sw: float):
         self._check(self.lib.dlma_set_params(self.h, float(m0), float(c_sw)))
+        self.params = (float(m0), float(c_sw))
 
     def dlma_apply_Dw(self, psi, prec: int = L.FP64):
         n = psi.shape[0]
@@ -215,41 +218,60 @@ class Context:
         self._check(self.lib.dlma_project(self.h, int(t), _ptr(V), N, _ptr(psi), n, _ptr(coeff), _mem(psi)))
         return coeff
 
+    @staticmethod
+    def _parts(out):
+        """The five correlator arrays of dlma_contract / dlma_correlators, as the library wrote them."""
+        return dict(zip(("C_dist", "C_rest", "C_mixed", "C_mixed_src", "C"), out))
+
+    @staticmethod
+    def _infos(info):
+        return [dict(iters_inner=i.iters_inner, iters_outer=i.iters_outer, true_resid=i.true_resid,
+                     converged=bool(i.converged)) for i in info]
+
     def dlma_contract(self, t_src: int, V, phi, n_noise: int):
         N = V.shape[1]
         _check_c128(V, (self.T, N, self.Vs, 3), "V")
         _check_c128(phi, (4 * N + 5 * n_noise, self.V, 4, 3), "phi")
-        out = [np.empty((4, self.T), dtype=np.complex128) for _ in range(3)]
+        out = [np.empty((4, self.T), dtype=np.complex128) for _ in range(5)]
         self._check(self.lib.dlma_contract(self.h, int(t_src), N, _ptr(V), int(n_noise), _ptr(phi),
-                                           _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _mem(phi)))
-        return {"C_dist": out[0], "C_rest": out[1], "C_mixed": out[2]}
+                                           *[_ptr(o) for o in out], _mem(phi)))
+        return self._parts(out)
 
     def dlma_correlators(self, t_src: int, N: int, eta, tol: float, inner: int = L.FP32):
+        """C_dist, C_rest, C_mixed, C_mixed_src and the Eq. 2 total C (all from the library)."""
         nn = eta.shape[0]
         _check_c128(eta, (nn, self.Vs, 4, 3), "eta")
-        out = [np.empty((4, self.T), dtype=np.complex128) for _ in range(3)]
+        out = [np.empty((4, self.T), dtype=np.complex128) for _ in range(5)]
         info = (L.SolveInfo * (4 * N + 5 * nn))()
         self._check(self.lib.dlma_correlators(self.h, int(t_src), int(N), nn, _ptr(eta), float(tol), inner,
-                                              _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), info, _mem(eta)))
-        res = {"C_dist": out[0], "C_rest": out[1], "C_mixed": out[2]}
-        res["C"] = res["C_rest"] + 2 * res["C_mixed"] + res["C_dist"]
-        res["info"] = [dict(iters_inner=i.iters_inner, iters_outer=i.iters_outer, true_resid=i.true_resid,
-                            converged=bool(i.converged)) for i in info]
+                                              *[_ptr(o) for o in out], info, _mem(eta)))
+        res = self._parts(out)
+        res["info"] = self._infos(info)
         return res
 
     def dlma_correlators_diluted(self, t_src: int, N: int, eta, tol: float, inner: int = L.FP32):
         """Colour x even-odd diluted wall sources, spin-explicit; eta complex [n_noise, L^3, 3]."""
         nn = eta.shape[0]
         _check_c128(eta, (nn, self.Vs, 3), "eta")
-        out = [np.empty((4, self.T), dtype=np.complex128) for _ in range(3)]
+        out = [np.empty((4, self.T), dtype=np.complex128) for _ in range(5)]
         info = (L.SolveInfo * (4 * N + 48 * nn))()
         self._check(self.lib.dlma_correlators_diluted(self.h, int(t_src), int(N), nn, _ptr(eta), float(tol), inner,
-                                                      _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), info, _mem(eta)))
-        res = {"C_dist": out[0], "C_rest": out[1], "C_mixed": out[2]}
-        res["C"] = res["C_rest"] + 2 * res["C_mixed"] + res["C_dist"]
-        res["info"] = [dict(iters_inner=i.iters_inner, iters_outer=i.iters_outer, true_resid=i.true_resid,
-                            converged=bool(i.converged)) for i in info]
+                                                      *[_ptr(o) for o in out], info, _mem(eta)))
+        res = self._parts(out)
+        res["info"] = self._infos(info)
         return res
+
+    def dlma_correlators_plain(self, t_src: int, eta, tol: float, inner: int = L.FP32):
+        """The plain stochastic estimator (no distillation): eta complex [n_noise, L^3, 4, 3]
+        (undiluted) or [n_noise, L^3, 3] (colour x even-odd diluted wall sources)."""
+        nn = eta.shape[0]
+        diluted = len(eta.shape) == 3
+        _check_c128(eta, (nn, self.Vs, 3) if diluted else (nn, self.Vs, 4, 3), "eta")
+        out = np.empty((4, self.T), dtype=np.complex128)
+        info = (L.SolveInfo * ((24 if diluted else 4) * nn))()
+        self._check(self.lib.dlma_correlators_plain(self.h, int(t_src), nn, _ptr(eta), int(diluted), float(tol),
+                                                    inner, _ptr(out), info, _mem(eta)))
+        return {"C": out, "info": self._infos(info)}
 
     def dlma_index_tables(self):
         eo = np.empty(self.V, dtype=np.int32)
@@ -261,6 +283,10 @@ class Context:
         return int(self.lib.dlma_kernel_launches(self.h))
 
     def dlma_last_timing(self):
-        out = np.zeros(3, dtype=np.float64)
-        self._check(self.lib.dlma_last_timing(self.h, _ptr(out)))
+        """The eight timing slots of the last call (meaning per call in include/dlma.h)."""
+        out = np.zeros(8, dtype=np.float64)
+        self._check(self.lib.dlma_last_timing(self.h, _ptr(out), 8))
         return out
+
+    def dlma_checkpoint_serial(self) -> int:
+        return int(self.lib.dlma_checkpoint_serial(self.h))

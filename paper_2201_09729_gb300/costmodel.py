@@ -47,9 +47,13 @@ def pays_off(c_dist_over_c: float, r1: int, r0: float) -> bool:
 
 
 def sweep(ctx, t_src: int, nc_list, eta, tol: float, inner: int, t_ratio: int | None = None):
-    """For each N_c: time the eigensolve of all timeslices and one source
-    timeslice's correlators (4 N_c + 5 n_noise solves), and evaluate Eqs. 6-9 for
-    the pseudoscalar channel at sink time t_ratio (default: T / 4 after t_src).
+    """For each N_c: time the eigensolve of all timeslices (split into its
+    Laplacian applications and its orthogonalisation, the two columns of
+    Table 2) and one source timeslice's correlators (4 N_c + 5 n_noise solves),
+    and evaluate Eqs. 6-9 for the pseudoscalar channel at sink time t_ratio
+    (default: T / 4 after t_src).  Every row also carries C_dist / C at every
+    sink time for the pseudoscalar and for the vector channel (the average of
+    gamma_1..3: the quantity Figs. 3 and 5 plot against the number of modes).
     eta: noise [n_noise, L^3, 4, 3] (numpy or a CUDA tensor)."""
     T = ctx.T
     tr = (t_src + T // 4) % T if t_ratio is None else t_ratio
@@ -57,17 +61,23 @@ def sweep(ctx, t_src: int, nc_list, eta, tol: float, inner: int, t_ratio: int | 
     rows = []
     for nc in nc_list:
         ctx.dlma_laplacian_eigs(-1, int(nc), 1e-10, want_vecs=False)
-        t_lap = float(ctx.dlma_last_timing()[0]) / 1e3
+        tm = ctx.dlma_last_timing()
+        t_lap = float(tm[0]) / 1e3
         r = ctx.dlma_correlators(t_src, int(nc), eta, tol, inner)
         t_corr = float(ctx.dlma_last_timing()[0]) / 1e3
         n_dist = 4 * int(nc)
         n_solves = n_dist + 5 * nn
         t_solve = t_corr / n_solves                # the paper's equal cost per source
         ratio = float(r["C_dist"][0][tr].real / r["C"][0][tr].real)
+        cv_dist = r["C_dist"][1:4].real.mean(axis=0)
+        cv = r["C"][1:4].real.mean(axis=0)
         r0 = r0_equivalent(t_lap, n_dist, t_solve, nn)
         rows.append({"Nc": int(nc), "N": n_dist, "R1": nn, "t_lap_s": t_lap, "t_solve_s": t_solve,
+                     "t_lap_matvec_s": float(tm[3]) / 1e3, "t_lap_ortho_s": float(tm[4]) / 1e3,
                      "C_dist_over_C_PS": ratio, "t": tr, "R0": r0, "R1_over_R0": nn / r0,
                      "bound_eq9": rest_fraction_bound(n_dist, nn), "pays_off": pays_off(ratio, nn, r0),
+                     "C_dist_over_C_PS_t": [float(x) for x in r["C_dist"][0].real / r["C"][0].real],
+                     "C_dist_over_C_V_t": [float(x) for x in cv_dist / cv],
                      "converged": all(i["converged"] for i in r["info"])})
     return rows
 

@@ -80,6 +80,9 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// slots of dlma_last_timing (meaning per call: see include/dlma.h)
+constexpr int kTimingSlots = 8;
+
 struct dlma_ctx {
   Geom g;
   int bc_t = 0;
@@ -90,13 +93,16 @@ struct dlma_ctx {
   uint64_t launches = 0;
   uint64_t memcap = 0;
   uint64_t work_bytes = 0;      // bytes currently held in work buffers
-  double timing[3] = {0, 0, 0};
+  double timing[kTimingSlots] = {0};
   // stencil block shape (sites x right-hand sides) per precision, chosen by autotune_hop
   int hop_sx[3] = {64, 64, 64}, hop_sy[3] = {4, 4, 4}, hop_tuned[3] = {0, 0, 0};
   int hop_l18[3] = {0, 0, 0};   // FP32: read 18-real links instead of rebuilding row 2
 
   bool have_gauge = false, have_params = false;
   double m0 = 0, csw = 0;
+  // generations of the gauge field and of the cached modes: a checkpoint taken
+  // under one generation is stale under the next
+  uint64_t gauge_gen = 0, eig_gen = 0;
 
   // gauge: U_mu(x) for x in parity p, SoA over the compressed site index
   double2* Ucan = nullptr;  // [V][4][3][3] canonical copy (clover build)
@@ -133,6 +139,9 @@ struct dlma_ctx {
   int checkpoint = 0;
   double* ckpt = nullptr;
   int ckpt_J = 0, ckpt_N = 0, ckpt_nn = 0, ckpt_tsrc = -1;
+  // state the checkpointed forward ran under, and its serial number (0: none)
+  double ckpt_m0 = 0, ckpt_csw = 0;
+  uint64_t ckpt_gauge_gen = 0, ckpt_eig_gen = 0, ckpt_serial = 0, ckpt_count = 0;
 
   // named work buffers
   DevBuf wb[64];
@@ -256,4 +265,53 @@ dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int 
 // per-context event timer helper
 struct EvTimer {
   cudaEvent_t a = nullptr, b = nullptr;
+};
+
+// Phase timer: events recorded on the context's stream at phase boundaries; the
+// time between consecutive marks is charged to the phase opened by the earlier
+// mark.  collect() (after a stream synchronisation) adds the elapsed times to
+// acc[phase] and recycles the events.
+struct PhaseTimer {
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, cudaEvent_t>> marks;
+  double acc[kTimingSlots] = {0};
+  int used = 0;
+  explicit PhaseTimer(cudaStream_t s) : st(s) {}
+  ~PhaseTimer() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+  void mark(int phase) {
+    if (used == (int)pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      pool.push_back(e);
+    }
+    cudaEvent_t e = pool[used++];
+    cudaEventRecord(e, st);
+    marks.push_back({phase, e});
+  }
+  // open `phase` unless it is already the open one
+  void enter(int phase) {
+    if (!marks.empty() && marks.back().first == phase) return;
+    mark(phase);
+  }
+  // the stream must have passed the last mark
+  void collect() {
+    for (size_t i = 0; i + 1 < marks.size(); i++) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, marks[i].second, marks[i + 1].second) == cudaSuccess && marks[i].first >= 0 &&
+          marks[i].first < kTimingSlots)
+        acc[marks[i].first] += ms;
+    }
+    if (!marks.empty()) {
+      // keep the last mark open: its phase continues
+      std::pair<int, cudaEvent_t> last = marks.back();
+      marks.clear();
+      for (int k = 0; k < used; k++)
+        if (pool[k] == last.second) { std::swap(pool[k], pool[0]); break; }
+      used = 1;
+      marks.push_back(last);
+    }
+  }
 };

@@ -12,6 +12,14 @@
 // M_r[alpha][beta] = sum_{x in t} conj(chi_r(x,alpha)) . phi_r(x,beta): the
 // Box(t) insertion at the sink only needs the projection coefficients, since
 // Box is diagonal in spin.
+//
+// The source-side mixed term (the second mixed contribution of Eq. 2, Box at the
+// source and 1 - Box at the sink) is exact, noise-free, from the distillation
+// solutions phi^{(k,beta)} = D^-1 (v_k (x) e_beta): with Box(t') = sum_{k,beta}
+// (v_k e_beta)(v_k e_beta)^dag,
+//   C^{1,Box'}(t) = sum_{k,beta,beta'} (G g5)_{beta' beta} <phi^{(k,beta)}, g5 G phi^{(k,beta')}>_t
+//   C_mixed_src(t) = C^{1,Box'}(t) - C_dist(t),
+// and the total of Eq. 2 is C = C_rest + 2 C_mixed + C_dist.
 #include "common.cuh"
 #include <algorithm>
 
@@ -394,6 +402,159 @@ __global__ void __launch_bounds__(128) k_noise_parts_dil(const double2* __restri
   }
 }
 
+// Per mode k and timeslice t: sum_{beta,beta'} B[beta'][beta] sum_{x in t} sum_{a,b}
+// A[a][b] conj(phi^{(k,beta)}(x,a,.)) . phi^{(k,beta')}(x,b,.) for the four channels
+// (A = g5 G, B = G g5).  The four solutions of mode k are rows 4 k .. 4 k + 3 of
+// psi (batch-relative).  Zero entries of A and B are skipped by uniform branches.
+__global__ void __launch_bounds__(128) k_src_box(const double2* __restrict__ psi, size_t stride_sites, int Vs,
+                                                 SpinMats S, int k0, double2* part, int T) {
+  const int t = blockIdx.x, kl = blockIdx.y;
+  Cx<double> acc[4];
+#pragma unroll
+  for (int ch = 0; ch < 4; ch++) acc[ch] = cx<double>(0, 0);
+  for (int m = threadIdx.x; m < Vs; m += blockDim.x) {
+    Cx<double> f[4][12];
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const double2* p = psi + ((size_t)(4 * kl + b) * stride_sites + (size_t)t * Vs + m) * 12;
+#pragma unroll
+      for (int q = 0; q < 12; q++) {
+        const double2 e = __ldg(p + q);
+        f[b][q] = cx<double>(e.x, e.y);
+      }
+    }
+#pragma unroll
+    for (int ch = 0; ch < 4; ch++)
+#pragma unroll
+      for (int bp = 0; bp < 4; bp++)
+#pragma unroll
+        for (int bt = 0; bt < 4; bt++) {
+          const Cx<double> Bv = cx<double>(S.re[4 + ch][bp][bt], S.im[4 + ch][bp][bt]);
+          if (Bv.re == 0.0 && Bv.im == 0.0) continue;
+          Cx<double> inner = cx<double>(0, 0);
+#pragma unroll
+          for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+              const Cx<double> Av = cx<double>(S.re[ch][a][b], S.im[ch][a][b]);
+              if (Av.re == 0.0 && Av.im == 0.0) continue;
+              Cx<double> d = cx<double>(0, 0);
+#pragma unroll
+              for (int c = 0; c < 3; c++) fma_conj_acc(d, f[bt][a * 3 + c], f[bp][b * 3 + c]);
+              fma_acc(inner, Av, d);
+            }
+          fma_acc(acc[ch], Bv, inner);
+        }
+  }
+  __shared__ double red[8][128];
+#pragma unroll
+  for (int ch = 0; ch < 4; ch++) {
+    red[2 * ch][threadIdx.x] = acc[ch].re;
+    red[2 * ch + 1][threadIdx.x] = acc[ch].im;
+  }
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int q = 0; q < 8; q++) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4)
+    part[((size_t)(k0 + kl) * 4 + threadIdx.x) * T + t] =
+        make_double2(red[2 * threadIdx.x][0], red[2 * threadIdx.x + 1][0]);
+}
+
+// out [5][4][T]: dist, rest, mixed (in), then mixed_src = sum_k part[k] - dist and
+// the total of Eq. 2, C = rest + 2 mixed + dist
+__global__ void k_totals(const double2* __restrict__ part, int N, int T, double2* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 4 * T) return;
+  const double2 d = out[e], r = out[4 * T + e], mx = out[8 * T + e];
+  double sr = 0, si = 0;
+  for (int k = 0; k < N; k++) {
+    const double2 v = part[(size_t)k * 4 * T + e];
+    sr += v.x;
+    si += v.y;
+  }
+  out[12 * T + e] = make_double2(sr - d.x, si - d.y);
+  out[16 * T + e] = make_double2(r.x + 2.0 * mx.x + d.x, r.y + 2.0 * mx.y + d.y);
+}
+
+// plain stochastic estimator, undiluted noise: rows 4 r + q of the solutions are
+// phi_r = D^-1 eta_r (q = 0) and chi_{r,k} = D^-1 g5 g_k eta_r (q = k);
+//   C[ch][t] = 1/N_r sum_r sum_{a,b} (g5 G)_{ab} M_r[ch][t][a][b],
+// M_r[ch] the spin inner products <chi, phi>_t (chi = phi_r for the pseudoscalar)
+__global__ void k_plain_parts(const double2* __restrict__ M, int T, int nn, SpinMats S, double2* out) {
+  const int t = blockIdx.x, ch = threadIdx.x;
+  if (ch >= 4) return;
+  Cx<double> s = cx<double>(0, 0);
+  for (int r = 0; r < nn; r++)
+    for (int a = 0; a < 4; a++)
+      for (int b = 0; b < 4; b++) {
+        const double2 mv = M[(((size_t)r * 4 + ch) * T + t) * 16 + a * 4 + b];
+        fma_acc(s, cx<double>(S.re[ch][a][b], S.im[ch][a][b]), cx<double>(mv.x, mv.y));
+      }
+  out[(size_t)ch * T + t] = make_double2(s.re / nn, s.im / nn);
+}
+
+// plain stochastic estimator, diluted wall sources: rows 24 r + 4 d + beta are
+// phi_{d,beta} = D^-1 (eta_d (x) e_beta);
+//   C[ch][t] = 1/N_r sum_{r,d} sum_{beta,beta'} B[beta][beta'] sum_{a,b} A[a][b] W[beta' a][beta b],
+// W from the spin inner products <phi_{d,beta'}, phi_{d,beta}>_t
+__global__ void k_plain_parts_dil(const double2* __restrict__ M, int T, int nn, SpinMats S, double2* out) {
+  const int t = blockIdx.x, ch = threadIdx.x;
+  if (ch >= 4) return;
+  Cx<double> s = cx<double>(0, 0);
+  for (int r = 0; r < nn; r++)
+    for (int d = 0; d < 6; d++)
+      for (int bq = 0; bq < 16; bq++) {
+        const int bp = bq / 4, bt = bq % 4;
+        const Cx<double> Bv = cx<double>(S.re[4 + ch][bt][bp], S.im[4 + ch][bt][bp]);
+        if (Bv.re == 0.0 && Bv.im == 0.0) continue;
+        Cx<double> sf = cx<double>(0, 0);
+        for (int a = 0; a < 4; a++)
+          for (int b = 0; b < 4; b++) {
+            const double2 mv = M[((((size_t)r * 6 + d) * 16 + bq) * T + t) * 16 + a * 4 + b];
+            fma_acc(sf, cx<double>(S.re[ch][a][b], S.im[ch][a][b]), cx<double>(mv.x, mv.y));
+          }
+        fma_acc(s, Bv, sf);
+      }
+  out[(size_t)ch * T + t] = make_double2(s.re / nn, s.im / nn);
+}
+
+// plain estimator sources, undiluted: row 4 r + q = eta_r (q = 0) or g5 g_q eta_r
+__global__ void k_sources_plain(int j0, int nb, int Vs, int t_src, const double2* __restrict__ eta, SpinMats S,
+                                double2* b, size_t stride_sites) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)nb * Vs) return;
+  const int m = (int)(e % Vs), jl = (int)(e / Vs), j = j0 + jl, r = j / 4, q = j % 4;
+  const double2* src = eta + ((size_t)r * Vs + m) * 12;
+  double2* out = b + ((size_t)jl * stride_sites + (size_t)t_src * Vs + m) * 12;
+  if (q == 0) {
+    for (int i = 0; i < 12; i++) out[i] = src[i];
+    return;
+  }
+  const int mi = 8 + (q - 1);   // g5 g_q
+  for (int a = 0; a < 4; a++)
+    for (int c = 0; c < 3; c++) {
+      Cx<double> s = cx<double>(0, 0);
+      for (int bb = 0; bb < 4; bb++)
+        fma_acc(s, cx<double>(S.re[mi][a][bb], S.im[mi][a][bb]), cx<double>(src[bb * 3 + c].x, src[bb * 3 + c].y));
+      out[a * 3 + c] = make_double2(s.re, s.im);
+    }
+}
+
+// plain estimator sources, diluted: row 24 r + 4 d + beta = eta_d (x) e_beta (pieces H of k_dilute)
+__global__ void k_sources_plain_dil(int j0, int nb, int Vs, int t_src, const double2* __restrict__ H, double2* b,
+                                    size_t stride_sites) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)nb * Vs) return;
+  const int m = (int)(e % Vs), jl = (int)(e / Vs), j = j0 + jl, rd = j / 4, beta = j % 4;
+  const double2* src = H + ((size_t)rd * Vs + m) * 12;   // spin 0 of the piece
+  double2* out = b + ((size_t)jl * stride_sites + (size_t)t_src * Vs + m) * 12;
+#pragma unroll
+  for (int c = 0; c < 3; c++) out[beta * 3 + c] = src[c];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -476,11 +637,38 @@ static dlma_status spin_inner(dlma_ctx* ctx, const double* psi, int nr, int base
   return DLMA_OK;
 }
 
+// copy the five [4][T] parts (dist, rest, mixed, mixed_src, total) to the host outputs
+static dlma_status fetch_parts(dlma_ctx* ctx, const double2* out, double* C_dist, double* C_rest, double* C_mixed,
+                               double* C_mixed_src, double* C_full) {
+  const int T = ctx->g.T;
+  std::vector<double2> h(20 * T);
+  CU(cudaMemcpyAsync(h.data(), out, sizeof(double2) * 20 * T, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  double* dst[5] = {C_dist, C_rest, C_mixed, C_mixed_src, C_full};
+  for (int q = 0; q < 5; q++)
+    if (dst[q]) memcpy(dst[q], h.data() + (size_t)q * 4 * T, sizeof(double2) * 4 * T);
+  return DLMA_OK;
+}
+
+// exact source-side Box terms of the distillation rows 4 k0 .. 4 (k0 + nk) - 1, which
+// are rows 0 .. 4 nk - 1 of psi: part[k][ch][t]
+static dlma_status src_box(dlma_ctx* ctx, const double* psi, int k0, int nk, double2* part) {
+  if (nk < 1) return DLMA_OK;
+  k_src_box<<<dim3(ctx->g.T, nk), 128, 0, ctx->stream>>>((const double2*)psi, (size_t)ctx->g.V, ctx->g.Vs,
+                                                         spin_mats(), k0, part, ctx->g.T);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+// C_dist, C_rest, C_mixed, C_mixed_src and the total C of Eq. 2 ([4][T] complex each,
+// HOST; the last two may be NULL) from the projection coefficients, the noise-pair
+// spin inner products and the source-side Box partials
 static dlma_status finish_contract(dlma_ctx* ctx, int N, int nn, const double2* coeff, const double2* M,
-                                   double* C_dist, double* C_rest, double* C_mixed) {
+                                   const double2* srcpart, double* C_dist, double* C_rest, double* C_mixed,
+                                   double* C_mixed_src, double* C_full) {
   const int T = ctx->g.T;
   double2* out;
-  TRY(workT(ctx, WS_CON, (size_t)12 * T, &out));
+  TRY(workT(ctx, WS_CON, (size_t)20 * T, &out));
   SpinMats S = spin_mats();
   k_cdist<<<dim3(T, 4), 256, 0, ctx->stream>>>(coeff, N, T, S, out);
   CHECK_LAUNCH();
@@ -490,13 +678,9 @@ static dlma_status finish_contract(dlma_ctx* ctx, int N, int nn, const double2* 
   } else {
     CU(cudaMemsetAsync(out + 4 * T, 0, sizeof(double2) * 8 * T, ctx->stream));
   }
-  std::vector<double2> h(12 * T);
-  CU(cudaMemcpyAsync(h.data(), out, sizeof(double2) * 12 * T, cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaStreamSynchronize(ctx->stream));
-  memcpy(C_dist, h.data(), sizeof(double2) * 4 * T);
-  memcpy(C_rest, h.data() + 4 * T, sizeof(double2) * 4 * T);
-  memcpy(C_mixed, h.data() + 8 * T, sizeof(double2) * 4 * T);
-  return DLMA_OK;
+  k_totals<<<(4 * T + 127) / 128, 128, 0, ctx->stream>>>(srcpart, N, T, out);
+  CHECK_LAUNCH();
+  return fetch_parts(ctx, out, C_dist, C_rest, C_mixed, C_mixed_src, C_full);
 }
 
 // ---------------------------------------------------------------------------
@@ -552,7 +736,7 @@ extern "C" dlma_status dlma_project(dlma_ctx* ctx, int t, const double* V, int N
 
 extern "C" dlma_status dlma_contract(dlma_ctx* ctx, int t_src, int N, const double* V, int n_noise,
                                      const double* phi, double* C_dist, double* C_rest, double* C_mixed,
-                                     dlma_mem mem) {
+                                     double* C_mixed_src, double* C_full, dlma_mem mem) {
   if (!ctx) return DLMA_ERR_INVALID_ARG;
   if (!V || !phi || !C_dist || !C_rest || !C_mixed || N < 1 || n_noise < 0 || t_src < 0 || t_src >= ctx->g.T)
     return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_contract");
@@ -573,29 +757,61 @@ extern "C" dlma_status dlma_contract(dlma_ctx* ctx, int t_src, int N, const doub
     TRY(workT(ctx, WS_T1, (size_t)n_noise * 4 * T * 16, &M));
     TRY(spin_inner(ctx, dphi + (size_t)4 * N * ctx->g.V * 24, n_noise, 0, M));
   }
+  double2* sp;
+  TRY(workT(ctx, WS_CON2, (size_t)N * 4 * T, &sp));
+  TRY(src_box(ctx, dphi, 0, N, sp));
   (void)t_src;
-  return finish_contract(ctx, N, n_noise, coeff, M, C_dist, C_rest, C_mixed);
+  return finish_contract(ctx, N, n_noise, coeff, M, sp, C_dist, C_rest, C_mixed, C_mixed_src, C_full);
+}
+
+// memory-bounded batch size of the correlator pipelines: two full complex128
+// fields per right-hand side plus the solver's work space
+static int pipeline_batch(dlma_ctx* ctx, int J, int granule) {
+  const size_t V = ctx->g.V;
+  const size_t per_rhs = V * 12 * 16 * 2 + field_bytes_per_rhs(DLMA_FP64, ctx->g.Vh) * 7 +
+                         field_bytes_per_rhs(DLMA_FP32, ctx->g.Vh) * 8;
+  size_t freeb = 0, totb = 0;
+  cudaMemGetInfo(&freeb, &totb);
+  const size_t budget = ctx->memcap ? ctx->memcap : (size_t)(0.8 * (double)freeb);
+  int nb = (int)std::max<size_t>((size_t)granule, std::min<size_t>((size_t)J, budget / per_rhs));
+  return std::min(nb, J);
+}
+
+static dlma_status check_modes(dlma_ctx* ctx, int N) {
+  if (ctx->eig_N != N) return set_err(ctx, DLMA_ERR_STATE, "no cached Laplacian modes for N = %d", N);
+  for (int t = 0; t < ctx->g.T; t++)
+    if (!ctx->eig_have[t]) return set_err(ctx, DLMA_ERR_STATE, "Laplacian modes of timeslice %d not computed", t);
+  return DLMA_OK;
+}
+
+// timing slots of the correlator pipelines
+constexpr int kPhSources = 1, kPhSolves = 2, kPhProject = 3, kPhContract = 4;
+
+static void store_phases(dlma_ctx* ctx, PhaseTimer& pt, float total_ms) {
+  for (int i = 0; i < kTimingSlots; i++) ctx->timing[i] = 0;
+  ctx->timing[0] = total_ms;
+  for (int q : {kPhSources, kPhSolves, kPhProject, kPhContract}) ctx->timing[q] = pt.acc[q];
 }
 
 extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* eta, double tol,
                                         dlma_prec inner, double* C_dist, double* C_rest, double* C_mixed,
-                                        dlma_solve_info* info, dlma_mem mem) {
+                                        double* C_mixed_src, double* C_full, dlma_solve_info* info, dlma_mem mem) {
   if (!ctx) return DLMA_ERR_INVALID_ARG;
   if (!ctx->have_gauge || !ctx->have_params) return set_err(ctx, DLMA_ERR_STATE, "gauge / params not set");
   if (N < 1 || n_noise < 0 || (n_noise && !eta) || t_src < 0 || t_src >= ctx->g.T || !(tol > 0) || !C_dist ||
       !C_rest || !C_mixed)
     return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_correlators");
-  if (ctx->eig_N != N) return set_err(ctx, DLMA_ERR_STATE, "no cached Laplacian modes for N = %d", N);
-  for (int t = 0; t < ctx->g.T; t++)
-    if (!ctx->eig_have[t]) return set_err(ctx, DLMA_ERR_STATE, "Laplacian modes of timeslice %d not computed", t);
+  TRY(check_modes(ctx, N));
   CU(cudaSetDevice(ctx->device));
-  const int T = ctx->g.T, Vs = ctx->g.Vs, n = 3 * Vs;
+  const int T = ctx->g.T, Vs = ctx->g.Vs;
   const size_t V = ctx->g.V;
   const int J = 4 * N + 5 * n_noise;
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   CU(cudaEventRecord(e0, ctx->stream));
+  PhaseTimer pt(ctx->stream);
+  pt.enter(kPhSources);
   const double* deta = nullptr;
   if (n_noise) TRY(copy_in(ctx, WS_ETA + 0, eta, (size_t)n_noise * Vs * 12 * 16, mem, &deta));
   // modes: all timeslices from the cache ([N][T] vectors) and the source timeslice
@@ -606,7 +822,7 @@ extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_n
   if (n_noise) {
     // copy eta out of the slot project_noise reuses
     double2* etac;
-    TRY(workT(ctx, WS_CON + 0, (size_t)n_noise * Vs * 12 + 12 * T, &etac));
+    TRY(workT(ctx, WS_CON + 0, (size_t)n_noise * Vs * 12 + 20 * T, &etac));
     CU(cudaMemcpyAsync(etac, deta, (size_t)n_noise * Vs * 12 * 16, cudaMemcpyDeviceToDevice, ctx->stream));
     deta = (const double*)etac;
     TRY(project_noise(ctx, VTs, N, deta, n_noise, &pe));
@@ -615,17 +831,15 @@ extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_n
   TRY(workT(ctx, WS_PROJ_C, (size_t)J * T * 4 * N, &coeff));
   double2* M = nullptr;
   if (n_noise) TRY(workT(ctx, WS_T1, (size_t)n_noise * 4 * T * 16, &M));
-  // batch size: two full complex128 fields per rhs plus the solver's work space
-  size_t per_rhs = V * 12 * 16 * 2 + field_bytes_per_rhs(DLMA_FP64, ctx->g.Vh) * 7 +
-                   field_bytes_per_rhs(DLMA_FP32, ctx->g.Vh) * 8;
-  size_t freeb = 0, totb = 0;
-  cudaMemGetInfo(&freeb, &totb);
-  size_t budget = ctx->memcap ? ctx->memcap : (size_t)(0.8 * (double)freeb);
-  int nb = (int)std::max<size_t>(5, std::min<size_t>((size_t)J, budget / per_rhs));
-  nb = std::min(nb, J);
+  double2* sp;
+  TRY(workT(ctx, WS_CON2, (size_t)N * 4 * T + (size_t)n_noise * 4 * N, &sp));
+  // project_noise keeps its coefficients at the start of WS_CON2: the partials follow them
+  sp += (size_t)n_noise * 4 * N;
+  const int nb = pipeline_batch(ctx, J, 5);
+  const int nb4 = std::max(4, (nb / 4) * 4);
   double *b, *x;
-  TRY(workT(ctx, WS_SRC, (size_t)nb * V * 24, &b));
-  TRY(workT(ctx, WS_SOL, (size_t)nb * V * 24, &x));
+  TRY(workT(ctx, WS_SRC, (size_t)std::max(nb, nb4) * V * 24, &b));
+  TRY(workT(ctx, WS_SOL, (size_t)std::max(nb, nb4) * V * 24, &x));
   // checkpoint (for dlma_correlators_backward): distillation solutions and phi_r, phibar_r
   const int J2 = 4 * N + 2 * n_noise;
   const size_t fbytes = V * 12 * 16;
@@ -643,22 +857,33 @@ extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_n
     ctx->ckpt_N = N;
     ctx->ckpt_nn = n_noise;
     ctx->ckpt_tsrc = t_src;
+    ctx->ckpt_m0 = ctx->m0;
+    ctx->ckpt_csw = ctx->csw;
+    ctx->ckpt_gauge_gen = ctx->gauge_gen;
+    ctx->ckpt_eig_gen = ctx->eig_gen;
+    ctx->ckpt_serial = ++ctx->ckpt_count;
   }
   dlma_status worst = DLMA_OK;
-  // distillation rows in chunks of nb, then noise rows in whole groups of 5
+  // distillation rows in chunks of whole modes (4 spins), then noise rows in whole groups of 5
   int j0 = 0;
   while (j0 < J) {
     int cnt;
-    if (j0 < 4 * N) cnt = std::min(nb, 4 * N - j0);
+    if (j0 < 4 * N) cnt = std::min(nb4, 4 * N - j0);
     else cnt = std::max(5, (nb / 5) * 5), cnt = std::min(cnt, J - j0);
+    pt.enter(kPhSources);
     TRY(sources_range(ctx, j0, cnt, N, t_src, VTs, deta, pe, b));
+    pt.enter(kPhSolves);
     dlma_status s = solve_fields(ctx, b, x, cnt, tol, inner, info ? info + j0 : nullptr);
     if (s != DLMA_OK && s != DLMA_ERR_NOT_CONVERGED) return s;
     if (s != DLMA_OK) worst = s;
+    pt.enter(kPhProject);
     TRY(project(ctx, VT, N, T, x, V, 0, cnt, coeff + (size_t)j0 * T * 4 * N));
+    pt.enter(kPhContract);
     if (j0 >= 4 * N) {
       int r0 = (j0 - 4 * N) / 5;
       TRY(spin_inner(ctx, x, cnt / 5, 0, M + (size_t)r0 * 4 * T * 16));
+    } else {
+      TRY(src_box(ctx, x, j0 / 4, cnt / 4, sp));
     }
     if (ctx->checkpoint) {
       if (j0 < 4 * N) {
@@ -673,12 +898,15 @@ extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_n
     }
     j0 += cnt;
   }
-  TRY(finish_contract(ctx, N, n_noise, coeff, M, C_dist, C_rest, C_mixed));
+  pt.enter(kPhContract);
+  TRY(finish_contract(ctx, N, n_noise, coeff, M, sp, C_dist, C_rest, C_mixed, C_mixed_src, C_full));
   CU(cudaEventRecord(e1, ctx->stream));
+  pt.mark(-1);
   CU(cudaStreamSynchronize(ctx->stream));
+  pt.collect();
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
-  ctx->timing[0] = ms;
+  store_phases(ctx, pt, ms);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return worst;
@@ -688,15 +916,14 @@ extern "C" dlma_status dlma_correlators(dlma_ctx* ctx, int t_src, int N, int n_n
 // diluted wall sources (Sec. 3): 4N distillation solves + 48 per noise vector
 extern "C" dlma_status dlma_correlators_diluted(dlma_ctx* ctx, int t_src, int N, int n_noise, const double* eta,
                                                 double tol, dlma_prec inner, double* C_dist, double* C_rest,
-                                                double* C_mixed, dlma_solve_info* info, dlma_mem mem) {
+                                                double* C_mixed, double* C_mixed_src, double* C_full,
+                                                dlma_solve_info* info, dlma_mem mem) {
   if (!ctx) return DLMA_ERR_INVALID_ARG;
   if (!ctx->have_gauge || !ctx->have_params) return set_err(ctx, DLMA_ERR_STATE, "gauge / params not set");
   if (N < 1 || n_noise < 1 || !eta || t_src < 0 || t_src >= ctx->g.T || !(tol > 0) || !C_dist || !C_rest ||
       !C_mixed)
     return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_correlators_diluted");
-  if (ctx->eig_N != N) return set_err(ctx, DLMA_ERR_STATE, "no cached Laplacian modes for N = %d", N);
-  for (int t = 0; t < ctx->g.T; t++)
-    if (!ctx->eig_have[t]) return set_err(ctx, DLMA_ERR_STATE, "Laplacian modes of timeslice %d not computed", t);
+  TRY(check_modes(ctx, N));
   CU(cudaSetDevice(ctx->device));
   const int T = ctx->g.T, Vs = ctx->g.Vs, L = ctx->g.L;
   const size_t V = ctx->g.V;
@@ -705,6 +932,8 @@ extern "C" dlma_status dlma_correlators_diluted(dlma_ctx* ctx, int t_src, int N,
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   CU(cudaEventRecord(e0, ctx->stream));
+  PhaseTimer pt(ctx->stream);
+  pt.enter(kPhSources);
   const double* deta;
   TRY(copy_in(ctx, WS_T0, eta, (size_t)nn * Vs * 3 * 16, mem, &deta));
   double2* H;
@@ -723,22 +952,22 @@ extern "C" dlma_status dlma_correlators_diluted(dlma_ctx* ctx, int t_src, int N,
   TRY(workT(ctx, WS_PROJ_C, (size_t)J * T * 4 * N, &coeff));
   double2* M;
   TRY(workT(ctx, WS_T1, (size_t)nn * 6 * 16 * T * 16, &M));
-  size_t per_rhs = V * 12 * 16 * 2 + field_bytes_per_rhs(DLMA_FP64, ctx->g.Vh) * 7 +
-                   field_bytes_per_rhs(DLMA_FP32, ctx->g.Vh) * 8;
-  size_t freeb = 0, totb = 0;
-  cudaMemGetInfo(&freeb, &totb);
-  size_t budget = ctx->memcap ? ctx->memcap : (size_t)(0.8 * (double)freeb);
-  int nb = (int)std::max<size_t>(48, std::min<size_t>((size_t)J, budget / per_rhs));
+  double2* sp;
+  TRY(workT(ctx, WS_CON2, (size_t)N * 4 * T + (size_t)6 * nn * 4 * N, &sp));
+  sp += (size_t)6 * nn * 4 * N;
+  const int nb = pipeline_batch(ctx, J, 48);
+  const int nb4 = std::max(4, (nb / 4) * 4);
   double *b, *x;
-  TRY(workT(ctx, WS_SRC, (size_t)nb * V * 24, &b));
-  TRY(workT(ctx, WS_SOL, (size_t)nb * V * 24, &x));
+  TRY(workT(ctx, WS_SRC, (size_t)std::max(nb, nb4) * V * 24, &b));
+  TRY(workT(ctx, WS_SOL, (size_t)std::max(nb, nb4) * V * 24, &x));
   std::vector<int> hp;
   dlma_status worst = DLMA_OK;
   int j0 = 0;
   while (j0 < J) {
     int cnt;
+    pt.enter(kPhSources);
     if (j0 < 4 * N) {
-      cnt = std::min(nb, 4 * N - j0);
+      cnt = std::min(nb4, 4 * N - j0);
       TRY(sources_range(ctx, j0, cnt, N, t_src, VTs, nullptr, nullptr, b));
     } else {
       cnt = std::min(std::max(48, (nb / 48) * 48), J - j0);
@@ -748,10 +977,13 @@ extern "C" dlma_status dlma_correlators_diluted(dlma_ctx* ctx, int t_src, int N,
                                                                           (double2*)b, V);
       CHECK_LAUNCH();
     }
+    pt.enter(kPhSolves);
     dlma_status st = solve_fields(ctx, b, x, cnt, tol, inner, info ? info + j0 : nullptr);
     if (st != DLMA_OK && st != DLMA_ERR_NOT_CONVERGED) return st;
     if (st != DLMA_OK) worst = st;
+    pt.enter(kPhProject);
     TRY(project(ctx, VT, N, T, x, V, 0, cnt, coeff + (size_t)j0 * T * 4 * N));
+    pt.enter(kPhContract);
     if (j0 >= 4 * N) {
       // spin inner products <phibar_{d,beta'}, phi_{d,beta}>_t of every piece in the batch
       const int r0 = (j0 - 4 * N) / 48, nr = cnt / 48;
@@ -770,28 +1002,140 @@ extern "C" dlma_status dlma_correlators_diluted(dlma_ctx* ctx, int t_src, int N,
       k_spin_inner<<<grid, 256, 0, ctx->stream>>>((const double2*)x, V, Vs, dp, M + (size_t)r0 * 6 * 16 * T * 16, T);
       CHECK_LAUNCH();
       CU(cudaStreamSynchronize(ctx->stream));     // hp is reused by the next batch
+    } else {
+      TRY(src_box(ctx, x, j0 / 4, cnt / 4, sp));
     }
     j0 += cnt;
   }
+  pt.enter(kPhContract);
   {
     double2* out;
-    TRY(workT(ctx, WS_CON2, (size_t)12 * T, &out));
+    TRY(workT(ctx, WS_OUT, (size_t)20 * T, &out));
     SpinMats S = spin_mats();
     k_cdist<<<dim3(T, 4), 256, 0, ctx->stream>>>(coeff, N, T, S, out);
     CHECK_LAUNCH();
     k_noise_parts_dil<<<dim3(T, 4), 128, 0, ctx->stream>>>(M, coeff, N, T, nn, 4 * N, S, out + 4 * T, out + 8 * T);
     CHECK_LAUNCH();
-    std::vector<double2> h(12 * T);
-    CU(cudaMemcpyAsync(h.data(), out, sizeof(double2) * 12 * T, cudaMemcpyDeviceToHost, ctx->stream));
+    k_totals<<<(4 * T + 127) / 128, 128, 0, ctx->stream>>>(sp, N, T, out);
+    CHECK_LAUNCH();
     CU(cudaEventRecord(e1, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    memcpy(C_dist, h.data(), sizeof(double2) * 4 * T);
-    memcpy(C_rest, h.data() + 4 * T, sizeof(double2) * 4 * T);
-    memcpy(C_mixed, h.data() + 8 * T, sizeof(double2) * 4 * T);
+    TRY(fetch_parts(ctx, out, C_dist, C_rest, C_mixed, C_mixed_src, C_full));
   }
+  pt.mark(-1);
+  CU(cudaStreamSynchronize(ctx->stream));
+  pt.collect();
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
-  ctx->timing[0] = ms;
+  store_phases(ctx, pt, ms);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return worst;
+}
+
+// ---------------------------------------------------------------------------
+// plain stochastic estimator of C (no distillation; the comparison of Fig. 1)
+extern "C" dlma_status dlma_correlators_plain(dlma_ctx* ctx, int t_src, int n_noise, const double* eta, int diluted,
+                                              double tol, dlma_prec inner, double* C, dlma_solve_info* info,
+                                              dlma_mem mem) {
+  if (!ctx) return DLMA_ERR_INVALID_ARG;
+  if (!ctx->have_gauge || !ctx->have_params) return set_err(ctx, DLMA_ERR_STATE, "gauge / params not set");
+  if (n_noise < 1 || !eta || !C || t_src < 0 || t_src >= ctx->g.T || !(tol > 0))
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "bad argument to dlma_correlators_plain");
+  CU(cudaSetDevice(ctx->device));
+  const int T = ctx->g.T, Vs = ctx->g.Vs, L = ctx->g.L;
+  const size_t V = ctx->g.V;
+  const int nn = n_noise;
+  const int per = diluted ? 24 : 4;          // solves per noise vector
+  const int J = per * nn;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, ctx->stream));
+  PhaseTimer pt(ctx->stream);
+  pt.enter(kPhSources);
+  const double* deta;
+  TRY(copy_in(ctx, WS_T0, eta, (size_t)nn * Vs * (diluted ? 3 : 12) * 16, mem, &deta));
+  double2* H = nullptr;
+  if (diluted) {
+    TRY(workT(ctx, WS_ETA, (size_t)nn * 6 * Vs * 12, &H));
+    const size_t tot = (size_t)nn * 6 * Vs;
+    k_dilute<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>((const double2*)deta, nn, L, t_src, H);
+    CHECK_LAUNCH();
+  } else {
+    double2* ec;
+    TRY(workT(ctx, WS_ETA, (size_t)nn * Vs * 12, &ec));
+    CU(cudaMemcpyAsync(ec, deta, (size_t)nn * Vs * 12 * 16, cudaMemcpyDeviceToDevice, ctx->stream));
+    deta = (const double*)ec;
+  }
+  const size_t npairs = diluted ? (size_t)nn * 6 * 16 : (size_t)nn * 4;
+  double2* M;
+  TRY(workT(ctx, WS_T1, npairs * T * 16, &M));
+  const int nb = pipeline_batch(ctx, J, per);
+  double *b, *x;
+  TRY(workT(ctx, WS_SRC, (size_t)nb * V * 24, &b));
+  TRY(workT(ctx, WS_SOL, (size_t)nb * V * 24, &x));
+  SpinMats S = spin_mats();
+  std::vector<int> hp;
+  dlma_status worst = DLMA_OK;
+  for (int j0 = 0; j0 < J;) {
+    const int cnt = std::min(std::max(per, (nb / per) * per), J - j0);
+    pt.enter(kPhSources);
+    CU(cudaMemsetAsync(b, 0, (size_t)cnt * V * 12 * 16, ctx->stream));
+    const size_t tot = (size_t)cnt * Vs;
+    if (diluted)
+      k_sources_plain_dil<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(j0, cnt, Vs, t_src, H,
+                                                                                (double2*)b, V);
+    else
+      k_sources_plain<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(j0, cnt, Vs, t_src,
+                                                                            (const double2*)deta, S, (double2*)b, V);
+    CHECK_LAUNCH();
+    pt.enter(kPhSolves);
+    dlma_status st = solve_fields(ctx, b, x, cnt, tol, inner, info ? info + j0 : nullptr);
+    if (st != DLMA_OK && st != DLMA_ERR_NOT_CONVERGED) return st;
+    if (st != DLMA_OK) worst = st;
+    pt.enter(kPhContract);
+    // spin inner products: undiluted <chi_{r,ch}, phi_r>, chi = phi_r (ch 0) or row 4 r + ch;
+    // diluted <phi_{d,beta'}, phi_{d,beta}> for every piece
+    const int ng = cnt / per, g0 = j0 / per;
+    hp.clear();
+    for (int r = 0; r < ng; r++) {
+      if (diluted) {
+        for (int d = 0; d < 6; d++)
+          for (int bq = 0; bq < 16; bq++) {
+            hp.push_back(24 * r + 4 * d + bq / 4);
+            hp.push_back(24 * r + 4 * d + bq % 4);
+          }
+      } else {
+        for (int ch = 0; ch < 4; ch++) {
+          hp.push_back(4 * r + ch);
+          hp.push_back(4 * r);
+        }
+      }
+    }
+    int* dp;
+    TRY(workT(ctx, WS_T2, hp.size(), &dp));
+    CU(cudaMemcpyAsync(dp, hp.data(), sizeof(int) * hp.size(), cudaMemcpyHostToDevice, ctx->stream));
+    const size_t moff = diluted ? (size_t)g0 * 6 * 16 : (size_t)g0 * 4;
+    k_spin_inner<<<dim3(T, (unsigned)(hp.size() / 2)), 256, 0, ctx->stream>>>((const double2*)x, V, Vs, dp,
+                                                                              M + moff * T * 16, T);
+    CHECK_LAUNCH();
+    CU(cudaStreamSynchronize(ctx->stream));     // hp is reused by the next batch
+    j0 += cnt;
+  }
+  pt.enter(kPhContract);
+  double2* out;
+  TRY(workT(ctx, WS_OUT, (size_t)4 * T, &out));
+  if (diluted) k_plain_parts_dil<<<T, 32, 0, ctx->stream>>>(M, T, nn, S, out);
+  else k_plain_parts<<<T, 32, 0, ctx->stream>>>(M, T, nn, S, out);
+  CHECK_LAUNCH();
+  CU(cudaEventRecord(e1, ctx->stream));
+  CU(cudaMemcpyAsync(C, out, sizeof(double2) * 4 * T, cudaMemcpyDeviceToHost, ctx->stream));
+  pt.mark(-1);
+  CU(cudaStreamSynchronize(ctx->stream));
+  pt.collect();
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  store_phases(ctx, pt, ms);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return worst;

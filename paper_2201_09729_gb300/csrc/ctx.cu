@@ -495,10 +495,14 @@ extern "C" dlma_status dlma_set_memory_cap(dlma_ctx* ctx, uint64_t bytes) {
 
 extern "C" uint64_t dlma_kernel_launches(const dlma_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-extern "C" dlma_status dlma_last_timing(const dlma_ctx* ctx, double* out3) {
-  if (!ctx || !out3) return DLMA_ERR_INVALID_ARG;
-  for (int i = 0; i < 3; i++) out3[i] = ctx->timing[i];
+extern "C" dlma_status dlma_last_timing(const dlma_ctx* ctx, double* out, int n) {
+  if (!ctx || !out || n < 0) return DLMA_ERR_INVALID_ARG;
+  for (int i = 0; i < n; i++) out[i] = i < kTimingSlots ? ctx->timing[i] : 0.0;
   return DLMA_OK;
+}
+
+extern "C" uint64_t dlma_checkpoint_serial(const dlma_ctx* ctx) {
+  return ctx && ctx->ckpt ? ctx->ckpt_serial : 0;
 }
 
 extern "C" dlma_status dlma_set_gauge(dlma_ctx* ctx, const double* links, dlma_mem mem) {
@@ -520,6 +524,7 @@ extern "C" dlma_status dlma_set_gauge(dlma_ctx* ctx, const double* links, dlma_m
   CU(cudaStreamSynchronize(ctx->stream));
   ctx->have_params = false;
   ctx->eig_N = 0;
+  ctx->gauge_gen++;
   if (h & 1) {
     ctx->have_gauge = false;
     return set_err(ctx, DLMA_ERR_NONFINITE, "gauge field holds NaN or Inf");

@@ -794,6 +794,7 @@ extern "C" dlma_status dlma_apply_schur(dlma_ctx* ctx, const double* in, double*
   CU(cudaStreamSynchronize(ctx->stream));
   float ms = 0;
   cudaEventElapsedTime(&ms, ev.a, ev.b);
+  for (int i = 0; i < kTimingSlots; i++) ctx->timing[i] = 0;
   ctx->timing[0] = ms;
   ctx->timing[1] = ms;
   ctx->timing[2] = 2;

@@ -159,9 +159,14 @@ extern "C" dlma_status dlma_set_checkpoint(dlma_ctx* ctx, int on) {
   if (!ctx) return DLMA_ERR_INVALID_ARG;
   ctx->checkpoint = on ? 1 : 0;
   if (!on) {
-    if (ctx->ckpt) cudaFree(ctx->ckpt);
+    if (ctx->ckpt) {
+      cudaSetDevice(ctx->device);
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->ckpt);
+    }
     ctx->ckpt = nullptr;
     ctx->ckpt_J = 0;
+    ctx->ckpt_serial = 0;
   }
   return DLMA_OK;
 }
@@ -176,6 +181,15 @@ extern "C" dlma_status dlma_correlators_backward(dlma_ctx* ctx, int t_src, int N
   if (!ctx->ckpt || ctx->ckpt_N != N || ctx->ckpt_nn != n_noise || ctx->ckpt_tsrc != t_src)
     return set_err(ctx, DLMA_ERR_STATE, "no checkpointed forward solutions for these arguments");
   if (ctx->eig_N != N) return set_err(ctx, DLMA_ERR_STATE, "no cached Laplacian modes for N = %d", N);
+  // the adjoint solves use the current operator and modes: they must be the ones
+  // the checkpointed forward ran with
+  if (!ctx->have_params || ctx->m0 != ctx->ckpt_m0 || ctx->csw != ctx->ckpt_csw)
+    return set_err(ctx, DLMA_ERR_STATE, "m0 / c_sw changed since the checkpointed forward (m0 %g -> %g, c_sw %g -> %g)",
+                   ctx->ckpt_m0, ctx->m0, ctx->ckpt_csw, ctx->csw);
+  if (ctx->gauge_gen != ctx->ckpt_gauge_gen)
+    return set_err(ctx, DLMA_ERR_STATE, "the gauge field changed since the checkpointed forward");
+  if (ctx->eig_gen != ctx->ckpt_eig_gen)
+    return set_err(ctx, DLMA_ERR_STATE, "the Laplacian modes were recomputed since the checkpointed forward");
   CU(cudaSetDevice(ctx->device));
   const int T = ctx->g.T, Vs = ctx->g.Vs;
   const size_t V = ctx->g.V;

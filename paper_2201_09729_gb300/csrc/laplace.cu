@@ -405,10 +405,19 @@ struct Eig {
   double *theta, *res, *coef, *scol;
   int* dropped;                  // [0] dropped directions of the last small_rr, [1 + 2t + {0,1}] Jacobi sweeps
   bool refilled = false;         // the last fetch refilled dropped columns
+  PhaseTimer* pt = nullptr;      // phases: kPhMatvec, kPhOrtho, kPhHost
   double drop_rel;
   uint64_t refill_seed;
   std::vector<double> th, rs;
 };
+
+// timing slots of dlma_laplacian_eigs (Table 2's split of the eigensolver time):
+// Laplacian applications, orthogonalisation (Gram matrices, small eigenproblems,
+// rotations, residuals, block conversions), host-side steps and transfers
+constexpr int kPhMatvec = 3, kPhOrtho = 4, kPhHost = 5;
+static inline void phase(Eig& E, int p) {
+  if (E.pt) E.pt->enter(p);
+}
 
 template <class R> static const typename LinkT<R>::T* links(dlma_ctx* ctx);
 template <> const double2* links<double>(dlma_ctx* ctx) { return ctx->U3; }
@@ -420,6 +429,7 @@ static dlma_status lap(Eig& E, const Cx<R>* in, const Cx<R>* prev, const Cx<floa
   dlma_ctx* ctx = E.ctx;
   const size_t total = (size_t)E.Tn * ctx->g.Vs * E.m;
   if (total >= (1ull << 31)) return set_err(ctx, DLMA_ERR_INVALID_ARG, "eigensolver block above 2^31 entries");
+  phase(E, kPhMatvec);
   k_lap<R><<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(ctx->g, E.t0, E.Tn, E.m, links<R>(ctx), in, prev,
                                                                      rin, scol, out, coef);
   CHECK_LAUNCH();
@@ -431,6 +441,7 @@ template <class R> static dlma_status gram(Eig& E, const Cx<R>* X, const Cx<R>* 
   dlma_ctx* ctx = E.ctx;
   const int tj = (E.m + GT - 1) / GT;
   const int tiles = herm ? tj * (tj + 1) / 2 : tj * tj;
+  phase(E, kPhOrtho);
   k_gram<R><<<dim3(tiles, E.nsplit, E.Tn), 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, herm, E.part);
   CHECK_LAUNCH();
   const size_t tot = (size_t)E.m * E.m * E.Tn;
@@ -441,6 +452,7 @@ template <class R> static dlma_status gram(Eig& E, const Cx<R>* X, const Cx<R>* 
 
 template <class R> static dlma_status rotate(Eig& E, const Cx<R>* X, Cx<R>* Z) {
   dlma_ctx* ctx = E.ctx;
+  phase(E, kPhOrtho);
   k_rotate<R><<<dim3((E.n + RT - 1) / RT, (E.m + RT - 1) / RT, E.Tn), 256, 0, ctx->stream>>>(X, E.C, E.n, E.m, Z);
   CHECK_LAUNCH();
   return DLMA_OK;
@@ -452,23 +464,12 @@ template <class T> static dlma_status small_rr(Eig& E) {
   const size_t sm = (size_t)3 * E.m * (E.m + 1) * sizeof(Cx<T>);   // three m x (m + 1) work matrices
   // the kernel also holds ~11 KB of static shared memory: always raise the dynamic limit
   const int use_smem = sm <= 200 * 1024;
+  phase(E, kPhOrtho);
   if (use_smem) CU(cudaFuncSetAttribute(k_small_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   CU(cudaMemsetAsync(E.dropped, 0, sizeof(int), ctx->stream));
   k_small_rr<T><<<E.Tn, 256, use_smem ? sm : 0, ctx->stream>>>(E.G, E.H, E.m, E.C, E.theta, (Cx<T>*)E.gwork,
                                                                use_smem, E.dropped, E.drop_rel);
   CHECK_LAUNCH();
-  if (getenv("DLMA_DEBUG_EIG")) {   // Jacobi sweeps of the two eigenproblems, per timeslice
-    std::vector<int> sw(2 * E.Tn);
-    CU(cudaMemcpyAsync(sw.data(), E.dropped + 1, sizeof(int) * 2 * E.Tn, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    int g0 = 1 << 30, g1 = 0, h0 = 1 << 30, h1 = 0;
-    for (int t = 0; t < E.Tn; t++) {
-      g0 = std::min(g0, sw[2 * t]); g1 = std::max(g1, sw[2 * t]);
-      h0 = std::min(h0, sw[2 * t + 1]); h1 = std::max(h1, sw[2 * t + 1]);
-    }
-    fprintf(stderr, "[eig] small_rr<%s> m=%d: Gram sweeps %d..%d, H sweeps %d..%d\n",
-            sizeof(T) == 4 ? "float" : "double", E.m, g0, g1, h0, h1);
-  }
   return DLMA_OK;
 }
 
@@ -483,6 +484,7 @@ static dlma_status rayleigh_ritz(Eig& E, Cx<R>* Y, Cx<R>* W, Cx<R>* Xout, Cx<R>*
   TRY(rotate<R>(E, Y, Xout));
   TRY(rotate<R>(E, W, AXout));
   dlma_ctx* ctx = E.ctx;
+  phase(E, kPhOrtho);
   k_resid<R><<<dim3((E.m + 31) / 32, E.Tn), 256, 0, ctx->stream>>>(Xout, AXout, E.theta, E.n, E.m, E.res, Rout);
   CHECK_LAUNCH();
   return DLMA_OK;
@@ -495,13 +497,16 @@ static dlma_status rayleigh_ritz(Eig& E, Cx<R>* Y, Cx<R>* W, Cx<R>* Xout, Cx<R>*
 template <class R> static dlma_status fetch(Eig& E, double* worst, Cx<R>* X) {
   dlma_ctx* ctx = E.ctx;
   const size_t cnt = (size_t)E.m * E.Tn;
+  phase(E, kPhHost);
   CU(cudaMemcpyAsync(E.th.data(), E.theta, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaMemcpyAsync(E.rs.data(), E.res, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
   int hdrop = 0;
   CU(cudaMemcpyAsync(&hdrop, E.dropped, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
+  if (E.pt) E.pt->collect();
   E.refilled = hdrop != 0;
   if (hdrop) {
+    phase(E, kPhOrtho);
     k_refill<R><<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X, E.theta, E.n, E.m, E.blk,
                                                                          E.refill_seed++);
     CHECK_LAUNCH();
@@ -589,9 +594,10 @@ static void cheb_coefficients(Eig& E, int d, std::vector<double>& hc, std::vecto
 }
 
 static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, double* lam_out,
-                             Cx<double>** Xres, int* m_out, int* iters_out) {
+                             Cx<double>** Xres, int* m_out, int* iters_out, PhaseTimer* pt) {
   Eig E;
   E.ctx = ctx;
+  E.pt = pt;
   E.t0 = t0;
   E.Tn = Tn;
   E.N = N;
@@ -639,10 +645,12 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   // plain A for the Rayleigh-Ritz W = A Y: coefficient slot d
   hc.assign(ncoef, 0.0);
   for (int t = 0; t < Tn; t++) hc[(size_t)d * 3 * Tn + 3 * t] = 1.0;
+  phase(E, kPhHost);
   CU(cudaMemcpyAsync(E.coef, hc.data(), sizeof(double) * ncoef, cudaMemcpyHostToDevice, ctx->stream));
   const double* plain = E.coef + (size_t)d * 3 * Tn;
 
   // ---- phase A: FP32 ----
+  phase(E, kPhOrtho);
   k_random<<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(E.F1, E.blk, 0x5eed2022ULL + (uint64_t)t0 * 7919ULL);
   CHECK_LAUNCH();
   // three FP32 blocks rotate: p3[0] = Ritz vectors X, p3[1], p3[2] free; F3 holds A X
@@ -664,6 +672,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
     // filtered block stays resolvable in single precision
     const int dA = safe_degree(E, 300.0, 20);
     cheb_coefficients(E, dA, hc, nullptr);
+    phase(E, kPhHost);
     CU(cudaMemcpyAsync(E.coef, hc.data(), sizeof(double) * ncoef, cudaMemcpyHostToDevice, ctx->stream));
     Cx<float>*prev = p3[0], *cur = p3[1], *nxt = p3[2];
     TRY(lap<float>(E, prev, nullptr, nullptr, nullptr, cur, E.coef));
@@ -685,6 +694,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   Cx<double> *X64 = E.D0, *W64 = E.D1, *Y64 = E.D2;
   // phase A's last Ritz pairs were not fetched, or hold refilled (random) columns
   const bool rr_first = E.refilled || it >= maxA;
+  phase(E, kPhOrtho);
   k_convert_block<float, double><<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X, rr_first ? Y64 : X64,
                                                                                            E.blk);
   CHECK_LAUNCH();
@@ -704,6 +714,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
     TRY(rayleigh_ritz<double>(E, Y64, W64, X64, Y64, R32, plain));
   } else {
     TRY(lap<double>(E, X64, nullptr, nullptr, nullptr, Y64, plain));
+    phase(E, kPhOrtho);
     k_resid<double><<<dim3((m + 31) / 32, Tn), 256, 0, ctx->stream>>>(X64, Y64, E.theta, E.n, m, E.res, R32);
     CHECK_LAUNCH();
   }
@@ -715,6 +726,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
     if (worst <= tol) { conv = true; break; }
     dB = safe_degree(E, 1e6, d);
     cheb_coefficients(E, dB, hc, &hs);
+    phase(E, kPhHost);
     CU(cudaMemcpyAsync(E.coef, hc.data(), sizeof(double) * ncoef, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(E.scol, hs.data(), sizeof(double) * nscol, cudaMemcpyHostToDevice, ctx->stream));
     // E_1 = a_1 R s_0 ; E_{k+1} = a_k A E_k + b_k E_k + c_k E_{k-1} + a_k R s_k
@@ -728,6 +740,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
       en = t;
     }
     // Y = (X s_d + E_d) / s_d column by column
+    phase(E, kPhOrtho);
     k_combine<<<(unsigned)((E.blk + 255) / 256), 256, 0, ctx->stream>>>(X64, ec, E.scol + (size_t)dB * Tn * m,
                                                                         (size_t)E.n * m, m, E.blk, Y64);
     CHECK_LAUNCH();
@@ -738,6 +751,7 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
     TRY(small_rr<double>(E));
     TRY(rotate<double>(E, Y64, X64));
     TRY(lap<double>(E, X64, nullptr, nullptr, nullptr, Y64, plain));   // A X, fresh (cheaper than W C)
+    phase(E, kPhOrtho);
     k_resid<double><<<dim3((m + 31) / 32, Tn), 256, 0, ctx->stream>>>(X64, Y64, E.theta, E.n, m, E.res, R32);
     CHECK_LAUNCH();
   }
@@ -789,12 +803,16 @@ extern "C" dlma_status dlma_laplacian_eigs(dlma_ctx* ctx, int t, int N, double t
   CU(cudaEventRecord(e0, ctx->stream));
   Cx<double>* X = nullptr;
   int m = 0, iters[2] = {0, 0};
-  dlma_status st = eig_batch(ctx, t0, Tn, N, tol, evals, &X, &m, iters);
+  PhaseTimer pt(ctx->stream);
+  pt.enter(kPhHost);
+  dlma_status st = eig_batch(ctx, t0, Tn, N, tol, evals, &X, &m, iters, &pt);
   if (st != DLMA_OK) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
   }
+  pt.enter(kPhHost);
+  ctx->eig_gen++;
   if (ctx->eig_N != N || !ctx->eig_V) {
     if (ctx->eig_V) cudaFree(ctx->eig_V);
     ctx->eig_V = nullptr;
@@ -821,11 +839,18 @@ extern "C" dlma_status dlma_laplacian_eigs(dlma_ctx* ctx, int t, int N, double t
   }
   CU(cudaEventRecord(e1, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
+  pt.mark(-1);
+  CU(cudaStreamSynchronize(ctx->stream));
+  pt.collect();
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
+  for (int i = 0; i < kTimingSlots; i++) ctx->timing[i] = 0;
   ctx->timing[0] = ms;
   ctx->timing[1] = iters[0];
   ctx->timing[2] = iters[1];
+  ctx->timing[kPhMatvec] = pt.acc[kPhMatvec];
+  ctx->timing[kPhOrtho] = pt.acc[kPhOrtho];
+  ctx->timing[kPhHost] = pt.acc[kPhHost];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return DLMA_OK;

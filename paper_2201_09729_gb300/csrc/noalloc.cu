@@ -7,8 +7,10 @@
 // cudaMalloc / cudaFree may imply in the middle of its own work.  For them
 // this entry point allocates nothing.  Its work space -- the packed input, the
 // odd-site intermediate T_oo^-1 D_oe in and the packed output -- lives in one
-// file-scope __device__ array of a fixed size that every GPU which loads the
-// library holds until the process exits.
+// file-scope __device__ array of a fixed size, held until the process exits by
+// every GPU that has loaded the library's device code.  That code is loaded
+// lazily, per device, so the array is reserved on a device by the first call
+// there (the same call that looks up its address, below).
 //
 // Host code cannot use the array's name as a device address (on the host it
 // names a stand-in object), so its device address is obtained once per device

@@ -520,25 +520,6 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   uint64_t graph_kernels = 0;
   dlma_status st = DLMA_OK;
   int it = 0;
-  // DLMA_DEBUG_SOLVE=1: print the per-rhs solver state of the first right-hand sides
-  const bool dbg = getenv("DLMA_DEBUG_SOLVE") != nullptr;
-  auto dump = [&](const char* where) {
-    const int n = std::min(nrhs, 3);
-    std::vector<double> rr(n), rn(n), al(n), sp(n);
-    std::vector<int> ac(n), av(n), r_(n), itv(n);
-    cudaMemcpy(rr.data(), B.sc.rr, sizeof(double) * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy(rn.data(), B.sc.rnorm, sizeof(double) * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy(al.data(), B.sc.alpha, sizeof(double) * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy(sp.data(), B.sc.stop2, sizeof(double) * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy(ac.data(), B.sc.active, sizeof(int) * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy(av.data(), B.sc.alive, sizeof(int) * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy(r_.data(), B.sc.ru, sizeof(int) * n, cudaMemcpyDeviceToHost);
-    cudaMemcpy(itv.data(), B.sc.iters, sizeof(int) * n, cudaMemcpyDeviceToHost);
-    for (int j = 0; j < n; j++)
-      fprintf(stderr, "[solve %s] j=%d it=%d rr=%.3e stop2=%.3e alpha=%.3e rnorm=%.3e active=%d alive=%d ru=%d\n",
-              where, j, itv[j], rr[j], sp[j], al[j], rn[j], ac[j], av[j], r_[j]);
-  };
-  if (dbg) dump("start");
   while (true) {
     if (!gexec) {
       const uint64_t l0 = ctx->launches;
@@ -562,10 +543,8 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
     ctx->launches += graph_kernels;
     it += chunk;
     CU(cudaStreamSynchronize(ctx->stream));
-    if (dbg) dump("chunk");
     if (hcount[1]) { st = set_err(ctx, DLMA_ERR_NONFINITE, "non-finite value in the solve"); break; }
     if (hcount[2] > 0) TRY((reliable_update<PB, PS>(ctx, B, nrhs, tol_target, delta2, false, PS == DLMA_FP16S)));
-    if (dbg && hcount[2] > 0) dump("update");
     k_count<<<1, 256, 0, ctx->stream>>>(B.sc.active, B.sc.ru, nrhs, B.sc.count);
     CHECK_LAUNCH();
     CU(cudaMemcpyAsync(hcount, B.sc.count, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -697,6 +676,7 @@ extern "C" dlma_status dlma_solve(dlma_ctx* ctx, const double* b, double* x, int
   CU(cudaStreamSynchronize(ctx->stream));
   float ms = 0;
   cudaEventElapsedTime(&ms, e0, e1);
+  for (int i = 0; i < kTimingSlots; i++) ctx->timing[i] = 0;
   ctx->timing[0] = ms;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

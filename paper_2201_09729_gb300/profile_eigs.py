@@ -4,7 +4,10 @@ field for profiling, e.g.
     ncu --metrics gpu__time_duration.sum --clock-control none --csv \\
         python -m paper_2201_09729_gb300.profile_eigs --L 16 --T 32 --N 32
 
-Prints the CUDA-event time and the FP32 / FP64 iteration counts of each run.
+Prints the CUDA-event time, the FP32 / FP64 iteration counts and the split
+of the time into Laplacian applications (matvec) and orthogonalisation
+(Gram matrices, small eigenproblems, rotations, residuals) of each run --
+the two columns of the paper's Table 2.
 """
 import argparse
 import os
@@ -33,9 +36,9 @@ def main():
     ctx.dlma_set_gauge(U)
     for r in range(a.reps):
         lam, _ = ctx.dlma_laplacian_eigs(-1, a.N, a.tol, want_vecs=False)
-        ms, it32, it64 = ctx.dlma_last_timing()
-        print(f"rep {r}: {ms:.1f} ms, iterations fp32 {int(it32)} fp64 {int(it64)}, "
-              f"lam[0] {lam[0, 0]:.6f} lam[N-1] {lam[0, -1]:.6f}")
+        ms, it32, it64, mv, ortho, host = ctx.dlma_last_timing()[:6]
+        print(f"rep {r}: {ms:.1f} ms (matvec {mv:.1f}, orthogonalisation {ortho:.1f}, host {host:.1f}), "
+              f"iterations fp32 {int(it32)} fp64 {int(it64)}, lam[0] {lam[0, 0]:.6f} lam[N-1] {lam[0, -1]:.6f}")
     ctx.close()
 
 

@@ -105,3 +105,56 @@ def test_correlator_gradients_differentiation_workload_fd(dl):
     fd = (loss_at(wl.m0, e0 + h * d) - loss_at(wl.m0, e0 - h * d)) / (2 * h)
     want = np.vdot(deta.ravel(), d.ravel()).real
     assert abs(fd - want) < 1e-5 * abs(want), (fd, want)
+
+
+def test_two_forwards_before_one_backward(dl):
+    # a loss summed over two masses and two noise draws: both forwards run before
+    # either backward, so each backward must restore its own m0 and recompute its
+    # replaced checkpoint; the gradients must equal those of the two losses taken
+    # one at a time (each against the oracle adjoint)
+    import torch
+
+    from paper_2201_09729_gb300.autograd import DLMACorrelatorPS, DLMASolve
+
+    wl = synth.WORKLOADS["plain_4c8"]
+    U, eta = synth.workload_inputs(wl)
+    w = synth.loss_weights(wl.T, synth.WEIGHT_SEED_BASE + wl.cfg)
+    ctx = dl.Context(wl.L, wl.T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    ctx.dlma_laplacian_eigs(-1, wl.n_modes, 1e-13, want_vecs=False)
+    V_all = np.stack([lap.lap_modes(lap.timeslice_links(U, wl.L, t), wl.L, wl.n_modes)[1] for t in range(wl.T)])
+    e_np = [np.ascontiguousarray(eta[0]), np.ascontiguousarray(synth.z2z2_noise(wl.n_noise, wl.vol_s, 611))]
+    m_vals = [wl.m0, wl.m0 + 0.05]
+    es = [torch.from_numpy(x).cuda().requires_grad_(True) for x in e_np]
+    ms = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in m_vals]
+    wt = torch.from_numpy(w).cuda()
+    cs = [DLMACorrelatorPS.apply(es[i], ms[i], ctx, wl.csw, 0, wl.n_modes, 1e-13, dl.FP64) for i in range(2)]
+    (torch.sum(wt * cs[0]) + torch.sum(wt * cs[1])).backward()
+    for i in range(2):
+        eo = dirac.EvenOdd(U, wl.L, wl.T, m_vals[i], wl.csw)
+        lo, dm0, deta = dlma.ps_loss_grads(solve.lu_solver(eo), solve.lu_solver_dag(eo), V_all, e_np[i], w,
+                                           wl.L, wl.T, 0)
+        assert abs(ms[i].grad.item() - dm0) < 1e-8 * abs(dm0), i
+        assert np.linalg.norm(es[i].grad.cpu().numpy() - deta) < 1e-8 * np.linalg.norm(deta), i
+    # the checkpoint is released after the backwards
+    assert ctx.dlma_checkpoint_serial() == 0
+    # a stale checkpoint is refused by the library: forward at one mass, backward at another
+    ctx.dlma_set_params(wl.m0, wl.csw)
+    ctx.dlma_set_checkpoint(True)
+    ctx.dlma_correlators(0, wl.n_modes, e_np[0], 1e-12, dl.FP64)
+    ctx.dlma_set_params(wl.m0 + 0.01, wl.csw)
+    with pytest.raises(dl.DlmaError) as exc:
+        ctx.dlma_correlators_backward(0, wl.n_modes, wl.n_noise, w, 1e-12, dl.FP64)
+    assert exc.value.status == 8
+    ctx.dlma_set_checkpoint(False)
+    # the solve's backward uses the operator of its own forward
+    L, T = wl.L, wl.T
+    b_h = synth.gaussian_spinors(1, L ** 3 * T, 612)
+    c_h = synth.gaussian_spinors(1, L ** 3 * T, 613)
+    b = torch.from_numpy(b_h).cuda().requires_grad_(True)
+    m = torch.tensor(0.2, dtype=torch.float64, requires_grad=True)
+    x = DLMASolve.apply(b, m, ctx, wl.csw, 1e-13, dl.FP64)
+    ctx.dlma_set_params(0.5, wl.csw)                       # changed between forward and backward
+    torch.sum(torch.conj(torch.from_numpy(c_h).cuda()) * x).real.backward()
+    y = solve.lu_solver_dag(dirac.EvenOdd(U, L, T, 0.2, wl.csw))(c_h)
+    assert np.linalg.norm(b.grad.cpu().numpy() - y) / np.linalg.norm(y) < 1e-10

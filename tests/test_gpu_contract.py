@@ -61,8 +61,10 @@ def test_contract_vs_oracle(dl):
     phi = np.concatenate([r["phi_dist"], r["phi_noise"].reshape(5 * nn, L ** 3 * T, 4, 3)])
     got = ctx.dlma_contract(0, np.ascontiguousarray(V_all), np.ascontiguousarray(phi), nn)
     scale = np.abs(r["C"]).max(axis=1, keepdims=True)
-    for key in ("C_dist", "C_rest", "C_mixed"):
+    for key in ("C_dist", "C_rest", "C_mixed", "C"):
         assert _close(got[key], r[key], scale, 1e-12), key
+    # the exact source-side mixed term from the distillation solutions
+    assert _close(got["C_mixed_src"], dlma.mixed_src(V_all, r["phi_dist"], L, T), scale, 1e-12)
 
 
 @pytest.mark.parametrize("prec,tol,ctol", [("FP64", 1e-12, 1e-10), ("FP32", 1e-10, 1e-8), ("FP16S", 1e-10, 1e-8)])
@@ -81,11 +83,14 @@ def test_pipeline_plain_workload(dl, prec, tol, ctol):
     V_all = np.stack([lap.lap_modes(lap.timeslice_links(U, wl.L, t), wl.L, wl.n_modes)[1] for t in range(wl.T)])
     ref = dlma.dlma_correlators(solve.lu_solver(eo), V_all, eta[0], wl.L, wl.T, 0)
     scale = np.abs(ref["C"]).max(axis=1, keepdims=True)
-    for key in ("C_dist", "C_rest", "C_mixed", "C"):
+    ref["C_mixed_src"] = dlma.mixed_src(V_all, ref["phi_dist"], wl.L, wl.T)
+    for key in ("C_dist", "C_rest", "C_mixed", "C_mixed_src", "C"):
         err = np.abs(res[key] - ref[key]).max(axis=1) / scale[:, 0]
         assert np.all(err <= ctol), (key, err)
     # pseudoscalar C_dist is tr[tau tau^dag]: real and positive
     assert np.all(res["C_dist"][0].real > 0)
+    # the total is the library's own C_rest + 2 C_mixed + C_dist
+    assert np.abs(res["C"] - (res["C_rest"] + 2 * res["C_mixed"] + res["C_dist"])).max() <= 1e-14 * scale.max()
 
 
 def test_pipeline_ragged_batches_with_memory_cap(dl):
@@ -101,5 +106,34 @@ def test_pipeline_ragged_batches_with_memory_cap(dl):
     V = L ** 3 * T
     ctx.dlma_set_memory_cap(int(7 * V * 12 * 16 * 6))
     capped = ctx.dlma_correlators(0, N, eta, 1e-11, dl.FP64)
-    for key in ("C_dist", "C_rest", "C_mixed"):
+    for key in ("C_dist", "C_rest", "C_mixed", "C_mixed_src", "C"):
         assert np.abs(capped[key] - full[key]).max() <= 1e-9 * np.abs(full["C"]).max()
+
+
+@pytest.mark.parametrize("prec,tol,ctol", [("FP64", 1e-12, 1e-10), ("FP32", 1e-10, 1e-8)])
+def test_plain_estimator_vs_oracle(dl, prec, tol, ctol):
+    # the plain stochastic estimator (no distillation, the comparison of Fig. 1):
+    # undiluted noise (4 solves per noise vector) and diluted wall sources (24 per
+    # noise vector) against the oracle with LU solves on the 4^3 x 8 workload
+    from oracle import dilution
+    wl = synth.WORKLOADS["plain_4c8"]
+    U, eta = synth.workload_inputs(wl)
+    ctx = dl.Context(wl.L, wl.T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    ctx.dlma_set_params(wl.m0, wl.csw)
+    eo = dirac.EvenOdd(U, wl.L, wl.T, wl.m0, wl.csw)
+    lu = solve.lu_solver(eo)
+    tp = 2
+    res = ctx.dlma_correlators_plain(tp, eta[0], tol, getattr(dl, prec))
+    assert len(res["info"]) == 4 * wl.n_noise and all(i["converged"] for i in res["info"])
+    nn = wl.n_noise
+    x = lu(dlma.plain_sources(eta[0], wl.L, wl.T, tp).reshape(4 * nn, wl.volume, 4, 3)).reshape(nn, 4, wl.volume, 4, 3)
+    want = dlma.plain_estimator(x[:, 0], x[:, 1:4], wl.L, wl.T)
+    err = np.abs(res["C"] - want).max(axis=1) / np.abs(want).max(axis=1)
+    assert np.all(err <= ctol), err
+    ew = synth.wall_noise(2, wl.vol_s, synth.NOISE_SEED_BASE + 200 + wl.cfg)
+    rd = ctx.dlma_correlators_plain(tp, ew, tol, getattr(dl, prec))
+    assert len(rd["info"]) == 48
+    want_d, _ = dilution.plain_diluted_correlators(lu, ew, wl.L, wl.T, tp)
+    err = np.abs(rd["C"] - want_d).max(axis=1) / np.abs(want_d).max(axis=1)
+    assert np.all(err <= ctol), err

@@ -28,3 +28,9 @@ def test_sweep_small_lattice():
         assert row["R0"] > 2 * row["R1"] + row["N"]
         assert np.isfinite(row["C_dist_over_C_PS"])
         assert row["pays_off"] == (1 - row["C_dist_over_C_PS"] <= row["R1_over_R0"])
+        # Table 2's split and the per-t ratios of both channels (Figs. 3 and 5)
+        assert row["t_lap_matvec_s"] > 0 and row["t_lap_ortho_s"] > 0
+        assert row["t_lap_matvec_s"] + row["t_lap_ortho_s"] <= 1.05 * row["t_lap_s"]
+        assert len(row["C_dist_over_C_V_t"]) == T and len(row["C_dist_over_C_PS_t"]) == T
+        assert row["C_dist_over_C_PS_t"][row["t"]] == pytest.approx(row["C_dist_over_C_PS"], rel=1e-12)
+        assert np.all(np.isfinite(row["C_dist_over_C_V_t"]))

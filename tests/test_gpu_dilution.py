@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import dilution, dirac
+from oracle import dilution, dirac, dlma
 from oracle import laplacian as lap
 from oracle import solve
 
@@ -39,7 +39,8 @@ def test_diluted_pipeline_plain_workload(dl, prec, tol, ctol):
     V_all = np.stack([lap.lap_modes(lap.timeslice_links(U, wl.L, t), wl.L, wl.n_modes)[1] for t in range(wl.T)])
     ref = dilution.diluted_correlators(solve.lu_solver(eo), V_all, eta, wl.L, wl.T, tp)
     scale = np.abs(ref["C"]).max(axis=1)
-    for key in ("C_dist", "C_rest", "C_mixed", "C"):
+    ref["C_mixed_src"] = dlma.mixed_src(V_all, ref["phi_dist"], wl.L, wl.T)
+    for key in ("C_dist", "C_rest", "C_mixed", "C_mixed_src", "C"):
         err = np.abs(res[key] - ref[key]).max(axis=1) / scale
         assert np.all(err <= ctol), (key, err)
     assert np.all(res["C_dist"][0].real > 0)
