@@ -62,6 +62,11 @@ typedef enum {
 
 typedef enum { DLMA_MEM_HOST = 0, DLMA_MEM_DEVICE = 1 } dlma_mem;
 
+typedef enum {
+  DLMA_SOLVER_CGNE = 0,      /* CG on the normal equations of the Schur system */
+  DLMA_SOLVER_BICGSTAB = 1   /* BiCGStab on the Schur system (FP32 inner solves; default) */
+} dlma_solver;
+
 typedef struct {
   int L;      /* spatial extent (even, >= 2) */
   int T;      /* temporal extent (even, >= 2) */
@@ -152,7 +157,8 @@ dlma_status dlma_apply_schur_noalloc(dlma_ctx* ctx, const double* in, double* ou
 /* dlma_solve: x = D^-1 b for nrhs full-lattice sources (complex
  * [nrhs][V][4][3]); the propagator solves of Eq. 4 and of the perambulator
  * (text after Eq. 3).  Even-odd Schur system, multi-RHS CG on the normal
- * equations; `inner` = DLMA_FP64 runs it in double precision, DLMA_FP32 /
+ * equations (or BiCGStab on the Schur system for FP32 inner solves, see
+ * dlma_set_solver); `inner` = DLMA_FP64 runs it in double precision, DLMA_FP32 /
  * DLMA_FP16S run the Krylov iteration in that precision (FP16: storage, FP32
  * arithmetic) with FP64 reliable updates: when a right-hand side's iterated
  * residual has dropped by a fixed factor since its last update, its solution
@@ -164,6 +170,18 @@ dlma_status dlma_apply_schur_noalloc(dlma_ctx* ctx, const double* in, double* ou
  * OOM, CUDA. */
 dlma_status dlma_solve(dlma_ctx* ctx, const double* b, double* x, int nrhs, double tol,
                        dlma_prec inner, dlma_solve_info* info, dlma_mem mem);
+
+/* dlma_set_solver: Krylov method of the inner solves with inner = DLMA_FP32
+ * (the FP64 and FP16S inner solves always run CGNE).  DLMA_SOLVER_BICGSTAB
+ * (the default) iterates BiCGStab on the Schur system Dhat x_e = bhat with
+ * FP32 vectors and the same FP64 reliable updates (residual replacement when
+ * |r| has dropped by 1e-3 since the last update; restart of the shadow
+ * residual after a breakdown or a stagnating update): two operator
+ * applications per iteration and about half as many as CGNE needs on these
+ * systems.  Right-hand sides it leaves above the tolerance are solved again
+ * with CGNE in the same call; their info sums both iteration counts.
+ * DLMA_SOLVER_CGNE selects CGNE throughout.  Errors: INVALID_ARG. */
+dlma_status dlma_set_solver(dlma_ctx* ctx, dlma_solver solver);
 
 /* dlma_solve_adjoint: y = D^-dag g for nrhs full-lattice fields, computed as
  * gamma_5 D^-1 gamma_5 g (gamma_5-hermiticity; the D^-1^dag of Eq. 3) with the

@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_CONVERGED", 3: "NONFINITE", 4
                 5: "OOM", 6: "CUDA", 7: "TIMEOUT", 8: "STATE"}
 FP64, FP32, FP16S = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
+SOLVER_CGNE, SOLVER_BICGSTAB = 0, 1
 
 
 class Lattice(C.Structure):
@@ -46,6 +47,7 @@ SIGNATURES = {
     "dlma_apply_schur": (_ST, [_P, _P, _P, _I, _I, _I, _I]),
     "dlma_apply_schur_noalloc": (_ST, [_P, _P, _P, _I, _I]),
     "dlma_solve": (_ST, [_P, _P, _P, _I, _D, _I, _P, _I]),
+    "dlma_set_solver": (_ST, [_P, _I]),
     "dlma_apply_laplacian": (_ST, [_P, _P, _P, _I, _I]),
     "dlma_laplacian_eigs": (_ST, [_P, _I, _I, _D, _P, _P, _I]),
     "dlma_make_sources": (_ST, [_P, _I, _I, _P, _I, _P, _P, _I]),

@@ -130,6 +130,10 @@ class Context:
         self._check(self.lib.dlma_apply_schur(self.h, _ptr(psi_e), _ptr(out), n, int(dagger), prec, _mem(psi_e)))
         return out
 
+    def dlma_set_solver(self, solver: int):
+        """L.SOLVER_BICGSTAB (default) or L.SOLVER_CGNE for the FP32 inner solves."""
+        self._check(self.lib.dlma_set_solver(self.h, int(solver)))
+
     def dlma_solve(self, b, tol: float, inner: int = L.FP64, allow_not_converged: bool = False):
         n = b.shape[0]
         _check_c128(b, (n, self.V, 4, 3), "b")

@@ -97,9 +97,11 @@ struct dlma_ctx {
   // stencil block shape (sites x right-hand sides) per precision, chosen by autotune_hop
   int hop_sx[3] = {64, 64, 64}, hop_sy[3] = {4, 4, 4}, hop_tuned[3] = {0, 0, 0};
   int hop_l18[3] = {0, 0, 0};   // FP32: read 18-real links instead of rebuilding row 2
+  int hop_nr[3] = {1, 1, 1};    // FP32: right-hand sides per thread (1 or 2)
 
   bool have_gauge = false, have_params = false;
   double m0 = 0, csw = 0;
+  int solver = DLMA_SOLVER_BICGSTAB;   // Krylov method of the FP32 inner solves
   // generations of the gauge field and of the cached modes: a checkpoint taken
   // under one generation is stale under the next
   uint64_t gauge_gen = 0, eig_gen = 0;
@@ -155,6 +157,7 @@ enum WorkSlot {
   WS_SCAL, WS_PART, WS_ACT, WS_ITERS,
   WS_EIG_X, WS_EIG_Y, WS_EIG_Y2, WS_EIG_W, WS_EIG_G, WS_EIG_PART, WS_EIG_S, WS_EIG_AUX,
   WS_PROJ_V, WS_PROJ_PART, WS_PROJ_C, WS_CON, WS_CON2, WS_SRC, WS_SOL, WS_ETA,
+  WS_BI_S, WS_BI_R0, WS_BI_PART, WS_BI_SCAL, WS_RETRY_B, WS_RETRY_X,
   WS_COUNT
 };
 
@@ -244,6 +247,10 @@ struct HopOp {
   void* cg_r = nullptr;
   const void* cg_p = nullptr;
   const double* cg_alpha = nullptr;
+  // DOT epilogue (Schur step B, no gamma_5 on the hop): per (rhs, site tile)
+  // partial of sum conj(w) out into dot_part; w is a field in the output precision
+  const struct Field* dot_w = nullptr;
+  double2* dot_part = nullptr;
 };
 dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Field* own, Field& out,
                        int* nblocks_out = nullptr);
@@ -253,6 +260,10 @@ int hop_grid_x(dlma_ctx* ctx, int prec);
 dlma_status schur_apply(dlma_ctx* ctx, const Field& in, Field& tmp, Field& out, int dagger,
                         const int* active, double* norm_part);
 dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, Field& out);
+// out = Dhat in with the partials of sum conj(w) out (dot_part, double2) and, if
+// norm_part is set, |out|^2 per (rhs, site tile)
+dlma_status schur_apply_dot(dlma_ctx* ctx, const Field& in, Field& tmp, Field& out, const int* active,
+                            const Field& w, double2* dot_part, double* norm_part);
 // z = Dhat^dag q fused with the CG update x += alpha p, r -= alpha z (x, r, p in the
 // vector precision); partial |r|^2 per (rhs, site tile) into part
 dlma_status schur_dag_cgupdate(dlma_ctx* ctx, const Field& q, Field& tmp, const int* active, Field& x, Field& r,

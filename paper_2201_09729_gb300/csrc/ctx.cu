@@ -495,6 +495,14 @@ extern "C" dlma_status dlma_set_memory_cap(dlma_ctx* ctx, uint64_t bytes) {
 
 extern "C" uint64_t dlma_kernel_launches(const dlma_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+extern "C" dlma_status dlma_set_solver(dlma_ctx* ctx, dlma_solver solver) {
+  if (!ctx) return DLMA_ERR_INVALID_ARG;
+  if (solver != DLMA_SOLVER_CGNE && solver != DLMA_SOLVER_BICGSTAB)
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "unknown solver %d", (int)solver);
+  ctx->solver = solver;
+  return DLMA_OK;
+}
+
 extern "C" dlma_status dlma_last_timing(const dlma_ctx* ctx, double* out, int n) {
   if (!ctx || !out || n < 0) return DLMA_ERR_INVALID_ARG;
   for (int i = 0; i < n; i++) out[i] = i < kTimingSlots ? ctx->timing[i] : 0.0;

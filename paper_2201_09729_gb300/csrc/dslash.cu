@@ -102,29 +102,21 @@ __device__ __forceinline__ void load_clover_block(const void* __restrict__ C, in
   }
 }
 
-// Work per thread: NR right-hand sides of one site (FP32 stencil), so each link is
-// loaded and reconstructed, and each clover block loaded, once for NR spinors.
-// The FP64 stencil is arithmetic-bound and the FP16 one register-bound: both keep
-// one.  MINB: resident blocks of 256 threads per SM the kernels are compiled for
-// (their register cap).  Measured on the 16^3 x 32 solve: NR = 1 with MINB = 3
-// and NR = 2 with MINB = 2 are within 2 % (NR = 2 speeds the plain operator by
-// 6 % but its CG variants spill); NR = 1 is the default.
-#ifndef DLMA_HOP_NR
-#define DLMA_HOP_NR 1
-#endif
-#ifndef DLMA_HOP_MINB
-#define DLMA_HOP_MINB 3
-#endif
+// Work per thread: NR right-hand sides of one site, so each link is loaded (and
+// rebuilt) and each clover block loaded once for NR spinors.  NR is a template
+// argument chosen per precision by the autotuner among {1, 2} for the FP32
+// stencil (the launches with the fused CG update always take NR = 1: their
+// epilogue holds three more spinors per right-hand side); the FP64 stencil is
+// arithmetic-bound and the FP16 one register-bound: both keep NR = 1.
+// hop_minb: resident blocks of 256 threads per SM the kernels are compiled for
+// (their register cap: 85 registers at 3, 128 at 2).
 // right-hand sides per chunk of the block order (see k_hop); on the 16^3 x 32 solve
 // 64 measured best of {16, 32, 64, unchunked}
 #ifndef DLMA_HOP_CHUNK
 #define DLMA_HOP_CHUNK 64
 #endif
 constexpr int kHopChunkRhs = DLMA_HOP_CHUNK;
-template <int P> struct HopCfg {
-  static constexpr int NR = P == DLMA_FP32 ? DLMA_HOP_NR : 1;
-  static constexpr int MINB = P == DLMA_FP32 ? DLMA_HOP_MINB : P == DLMA_FP64 ? 2 : 3;
-};
+constexpr int hop_minb(int P, int NR) { return P == DLMA_FP64 ? 2 : (NR > 1 ? 2 : 3); }
 
 // ---------------------------------------------------------------------------
 struct HopArgs {
@@ -146,6 +138,8 @@ struct HopArgs {
   // block order (1D grid): chunks of right-hand-side groups (slowest), site tiles,
   // groups within the chunk (fastest)
   int ntiles, ngroups, gpc;
+  // DOT epilogue: per (rhs, tile) partial of sum conj(w) out (complex) next to |out|^2
+  const void* dot_w; const float* dot_w_scale; double2* dot_part;
 };
 
 template <class R>
@@ -258,10 +252,10 @@ __device__ __forceinline__ R cg_update(void* __restrict__ x, void* __restrict__ 
   return n;
 }
 
-template <int P, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM, bool L18, bool CGU = false>
-__global__ void __launch_bounds__(256, HopCfg<P>::MINB) k_hop(HopArgs a) {
+template <int P, int NR, bool G5IN, bool G5HOP, int OWN, bool KOUT, bool HOP, bool NORM, bool L18, bool CGU = false,
+          bool DOT = false>
+__global__ void __launch_bounds__(256, hop_minb(P, NR)) k_hop(HopArgs a) {
   typedef typename PT<P>::R R;
-  constexpr int NR = HopCfg<P>::NR;
   // Block order: the right-hand sides of a chunk (gpc groups, about 32 rhs) run back
   // to back on a site tile, so its links and clover come from DRAM once per chunk
   // and from L2 otherwise; the chunk sweeps all tiles before the next chunk starts,
@@ -288,8 +282,9 @@ __global__ void __launch_bounds__(256, HopCfg<P>::MINB) k_hop(HopArgs a) {
 #pragma unroll
   for (int q = 0; q < NR; q++) jl[q] = vq[q] ? jq[q] : jany;
   R nrm[NR];   // |out|^2 per thread in the stencil precision; block partials in FP64
+  R dre[NR], dim[NR];   // DOT: sum conj(w) out
 #pragma unroll
-  for (int q = 0; q < NR; q++) nrm[q] = 0;
+  for (int q = 0; q < NR; q++) nrm[q] = dre[q] = dim[q] = 0;
   if (valid) {
     Spinor<R> res[NR];
 #pragma unroll
@@ -425,28 +420,57 @@ __global__ void __launch_bounds__(256, HopCfg<P>::MINB) k_hop(HopArgs a) {
 #pragma unroll
             for (int c = 0; c < 3; c++) nrm[q] += norm2(res[q].c[s][c]);
         }
+        if (DOT) {
+          const Spinor<R> w = load_spinor<P>((const char*)a.dot_w + (size_t)j * a.out_stride,
+                                             a.dot_w_scale ? a.dot_w_scale + (size_t)j * g.Vh : nullptr, g.Vh, i);
+#pragma unroll
+          for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+              const Cx<R> wv = w.c[s][c], ov = res[q].c[s][c];
+              dre[q] = fma(wv.re, ov.re, fma(wv.im, ov.im, dre[q]));
+              dim[q] = fma(wv.re, ov.im, fma(-wv.im, ov.re, dim[q]));
+            }
+        }
       }
     }
   }
-  if (NORM) {
+  if (NORM || DOT) {
     // per (rhs, block) partial sums: the warps of one threadIdx.y row share NR rhs
-    __shared__ double red[32 * NR];
+    __shared__ double red[3][32 * NR];
     const int wx = threadIdx.x >> 5, nwx = blockDim.x >> 5;
 #pragma unroll
     for (int q = 0; q < NR; q++) {
-      R v = nrm[q];
+      R v = nrm[q], vr = dre[q], vi = dim[q];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) red[(threadIdx.y * nwx + wx) * NR + q] = (double)v;
+      for (int o = 16; o > 0; o >>= 1) {
+        if (NORM) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (DOT) {
+          vr += __shfl_down_sync(0xffffffffu, vr, o);
+          vi += __shfl_down_sync(0xffffffffu, vi, o);
+        }
+      }
+      if ((threadIdx.x & 31) == 0) {
+        const int slot = (threadIdx.y * nwx + wx) * NR + q;
+        red[0][slot] = (double)v;
+        red[1][slot] = (double)vr;
+        red[2][slot] = (double)vi;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int q = 0; q < NR; q++) {
         if (jq[q] >= a.nrhs) continue;
-        double t = 0;
-        for (int w = 0; w < nwx; w++) t += red[(threadIdx.y * nwx + w) * NR + q];
-        a.norm_part[(size_t)jq[q] * a.ntiles + tile] = t;
+        double t = 0, tr = 0, ti = 0;
+        for (int w = 0; w < nwx; w++) {
+          const int slot = (threadIdx.y * nwx + w) * NR + q;
+          t += red[0][slot];
+          tr += red[1][slot];
+          ti += red[2][slot];
+        }
+        if (NORM) a.norm_part[(size_t)jq[q] * a.ntiles + tile] = t;
+        if (DOT) a.dot_part[(size_t)jq[q] * a.ntiles + tile] = make_double2(tr, ti);
       }
     }
   }
@@ -467,18 +491,14 @@ int hop_grid_x(dlma_ctx* ctx, int prec) {
   return (ctx->g.Vh + sx - 1) / sx;
 }
 
-template <int P, bool L18>
+template <int P, int NR, bool L18>
 static void dispatch(const HopOp& op, dim3 grid, dim3 blk, cudaStream_t st, const HopArgs& a) {
   const bool norm = op.norm_part != nullptr;
-#define L(G5I, G5H, OWN, KO, HOP, NRM) k_hop<P, G5I, G5H, OWN, KO, HOP, NRM, L18><<<grid, blk, 0, st>>>(a)
+#define L(G5I, G5H, OWN, KO, HOP, NRM) k_hop<P, NR, G5I, G5H, OWN, KO, HOP, NRM, L18><<<grid, blk, 0, st>>>(a)
   if (!op.hop) {                                   // Kout * (Kown * own)
     if (op.own == 1 && op.kout) L(false, false, 1, true, false, false);
     else if (op.own == 2 && !op.kout) L(false, false, 2, false, false, false);
     else L(false, false, 1, false, false, false);
-    return;
-  }
-  if (op.cg_x) {                                   // Schur step B of the adjoint + CG update
-    k_hop<P, false, true, 2, false, true, true, L18, true><<<grid, blk, 0, st>>>(a);
     return;
   }
   if (op.own == 0 && op.kout) {                    // Schur step A (and its dagger)
@@ -495,6 +515,12 @@ static void dispatch(const HopOp& op, dim3 grid, dim3 blk, cudaStream_t st, cons
     L(false, false, 0, false, true, false);
   }
 #undef L
+}
+
+// Schur step B of the adjoint with the fused CG update (one right-hand side per thread)
+template <int P, bool L18>
+static void dispatch_cgu(dim3 grid, dim3 blk, cudaStream_t st, const HopArgs& a) {
+  k_hop<P, 1, false, true, 2, false, true, true, L18, true><<<grid, blk, 0, st>>>(a);
 }
 
 dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Field* own, Field& out,
@@ -524,6 +550,9 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   a.cg_p = op.cg_p;
   a.cg_alpha = op.cg_alpha;
   a.cg_stride = field_units_per_rhs(P == DLMA_FP64 ? DLMA_FP64 : DLMA_FP32, ctx->g.Vh) * 16;
+  a.dot_w = op.dot_w ? op.dot_w->data : nullptr;
+  a.dot_w_scale = op.dot_w ? op.dot_w->scale : nullptr;
+  a.dot_part = op.dot_part;
   const size_t Vh = ctx->g.Vh;
   const int p = op.p_out;
   const void* Kown = nullptr;
@@ -548,17 +577,45 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   int sx, sy;
   hop_block(ctx, P, sx, sy);
   dim3 blk(sx, sy);
-  const int nr = P == DLMA_FP32 ? HopCfg<DLMA_FP32>::NR : 1;
+  const bool cgu = op.cg_x != nullptr && op.hop;
+  const bool dot = op.dot_part != nullptr && op.hop && op.own == 2 && !op.kout && !op.g5_hop;
+  const int nr = (P == DLMA_FP32 && !cgu) ? ctx->hop_nr[P] : 1;
   a.ntiles = (ctx->g.Vh + sx - 1) / sx;
   a.ngroups = (out.nrhs + sy * nr - 1) / (sy * nr);
   a.gpc = std::max(1, std::min(a.ngroups, kHopChunkRhs / (sy * nr)));
   const int nchunks = (a.ngroups + a.gpc - 1) / a.gpc;
   dim3 grid((unsigned)((size_t)nchunks * a.ntiles * a.gpc));
   if (nblocks_out) *nblocks_out = a.ntiles;
-  if (P == DLMA_FP64) dispatch<DLMA_FP64, false>(op, grid, blk, ctx->stream, a);
-  else if (P == DLMA_FP32 && a.l18) dispatch<DLMA_FP32, true>(op, grid, blk, ctx->stream, a);
-  else if (P == DLMA_FP32) dispatch<DLMA_FP32, false>(op, grid, blk, ctx->stream, a);
-  else dispatch<DLMA_FP16S, false>(op, grid, blk, ctx->stream, a);
+  cudaStream_t st = ctx->stream;
+  if (dot) {
+    // Schur step B with the DOT epilogue (and |out|^2 when norm_part is set)
+    const bool nrm = op.norm_part != nullptr;
+#define LD(PP, NRR, LL) \
+  (nrm ? k_hop<PP, NRR, false, false, 2, false, true, true, LL, false, true><<<grid, blk, 0, st>>>(a) \
+       : k_hop<PP, NRR, false, false, 2, false, true, false, LL, false, true><<<grid, blk, 0, st>>>(a))
+    if (P == DLMA_FP64) LD(DLMA_FP64, 1, false);
+    else if (P == DLMA_FP32 && nr == 2) { if (a.l18) LD(DLMA_FP32, 2, true); else LD(DLMA_FP32, 2, false); }
+    else if (P == DLMA_FP32) { if (a.l18) LD(DLMA_FP32, 1, true); else LD(DLMA_FP32, 1, false); }
+    else LD(DLMA_FP16S, 1, false);
+#undef LD
+  } else if (cgu) {
+    if (P == DLMA_FP64) dispatch_cgu<DLMA_FP64, false>(grid, blk, st, a);
+    else if (P == DLMA_FP32 && a.l18) dispatch_cgu<DLMA_FP32, true>(grid, blk, st, a);
+    else if (P == DLMA_FP32) dispatch_cgu<DLMA_FP32, false>(grid, blk, st, a);
+    else dispatch_cgu<DLMA_FP16S, false>(grid, blk, st, a);
+  } else if (P == DLMA_FP64) {
+    dispatch<DLMA_FP64, 1, false>(op, grid, blk, st, a);
+  } else if (P == DLMA_FP32) {
+    if (nr == 2) {
+      if (a.l18) dispatch<DLMA_FP32, 2, true>(op, grid, blk, st, a);
+      else dispatch<DLMA_FP32, 2, false>(op, grid, blk, st, a);
+    } else {
+      if (a.l18) dispatch<DLMA_FP32, 1, true>(op, grid, blk, st, a);
+      else dispatch<DLMA_FP32, 1, false>(op, grid, blk, st, a);
+    }
+  } else {
+    dispatch<DLMA_FP16S, 1, false>(op, grid, blk, st, a);
+  }
   CHECK_LAUNCH();
   return DLMA_OK;
 }
@@ -572,18 +629,26 @@ dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, F
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bx = ctx->hop_sx[prec], by = ctx->hop_sy[prec], bl = 0;
-  // FP32: also try 18-real links; DLMA_FORCE_LINKS=12 / 18 pins the format (tests)
+  int bx = ctx->hop_sx[prec], by = ctx->hop_sy[prec], bl = 0, bn = 1;
+  // FP32: also try 18-real links and two right-hand sides per thread;
+  // DLMA_FORCE_LINKS=12 / 18 and DLMA_FORCE_NR=1 / 2 pin the choice (tests)
   int l0 = 0, l1 = prec == DLMA_FP32 ? 1 : 0;
+  int n0 = 1, n1 = prec == DLMA_FP32 ? 2 : 1;
   if (const char* f = getenv("DLMA_FORCE_LINKS")) {
     if (prec == DLMA_FP32 && atoi(f) == 18) l0 = l1 = 1;
     if (atoi(f) == 12) l0 = l1 = 0;
   }
+  if (const char* f = getenv("DLMA_FORCE_NR")) {
+    if (prec == DLMA_FP32 && atoi(f) == 2) n0 = n1 = 2;
+    if (atoi(f) == 1) n0 = n1 = 1;
+  }
+  for (int nr = n0; nr <= n1; nr++)
   for (int l = l0; l <= l1; l++)
   for (const auto& c : cand) {
     ctx->hop_sx[prec] = c[0];
     ctx->hop_sy[prec] = c[1];
     ctx->hop_l18[prec] = l;
+    ctx->hop_nr[prec] = nr;
     float tot = 0;
     for (int r = 0; r < 3; r++) {
       CU(cudaEventRecord(e0, ctx->stream));
@@ -594,11 +659,12 @@ dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, F
       CU(cudaEventElapsedTime(&ms, e0, e1));
       if (r > 0) tot += ms;
     }
-    if (tot < best) { best = tot; bx = c[0]; by = c[1]; bl = l; }
+    if (tot < best) { best = tot; bx = c[0]; by = c[1]; bl = l; bn = nr; }
   }
   ctx->hop_sx[prec] = bx;
   ctx->hop_sy[prec] = by;
   ctx->hop_l18[prec] = bl;
+  ctx->hop_nr[prec] = bn;
   ctx->hop_tuned[prec] = 1;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -628,6 +694,27 @@ dlma_status schur_dag_cgupdate(dlma_ctx* ctx, const Field& q, Field& tmp, const 
   B.cg_alpha = alpha;
   Field dummy = q;      // output not stored: the CG epilogue consumes it
   TRY(launch_hop(ctx, B, tmp, &q, dummy));
+  return DLMA_OK;
+}
+
+dlma_status schur_apply_dot(dlma_ctx* ctx, const Field& in, Field& tmp, Field& out, const int* active,
+                            const Field& w, double2* dot_part, double* norm_part) {
+  HopOp A;
+  A.p_out = 1;
+  A.own = 0;
+  A.kout = 3;
+  A.active = active;
+  TRY(launch_hop(ctx, A, in, nullptr, tmp));
+  HopOp B;
+  B.p_out = 0;
+  B.own = 2;
+  B.kout = 0;
+  B.s = -1.0;
+  B.active = active;
+  B.norm_part = norm_part;
+  B.dot_w = &w;
+  B.dot_part = dot_part;
+  TRY(launch_hop(ctx, B, tmp, &in, out));
   return DLMA_OK;
 }
 

@@ -301,6 +301,304 @@ __global__ void k_resume(int nrhs, CgScal sc, double delta2) {
   sc.active[j] = 1;
 }
 
+// ---- BiCGStab (complex, per right-hand side) --------------------------------
+// Per-rhs complex scalars of the BiCGStab recursion
+struct BiScal {
+  double2* rho;     // (r0, r)
+  double2* alpha;
+  double2* omega;
+  double2* beta;
+  int* brk;         // breakdown seen: restart the shadow residual at the next update
+};
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// a breakdown pauses the rhs for an FP64 update that restarts its shadow residual
+__device__ __forceinline__ void bi_breakdown(int j, CgScal& sc, BiScal& bs) {
+  sc.active[j] = 0;
+  sc.ru[j] = 1;
+  bs.brk[j] = 1;
+}
+
+// alpha = rho / (r0, v)   (one warp per rhs over the stencil's DOT partials)
+__global__ void k_bi_alpha(const double2* dpart, int nb, int nrhs, CgScal sc, BiScal bs) {
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (j >= nrhs || !sc.active[j]) return;
+  const int lane = threadIdx.x & 31;
+  double2 s = make_double2(0, 0);
+  for (int b = lane; b < nb; b += 32) {
+    const double2 v = dpart[(size_t)j * nb + b];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  s = warp_sum2(s);
+  if (lane == 0) {
+    const double2 a = cdiv(bs.rho[j], s);
+    const bool ok = (s.x != 0.0 || s.y != 0.0) && cfinite(s) && cfinite(a);
+    bs.alpha[j] = ok ? a : make_double2(0, 0);
+    if (!ok) {
+      bi_breakdown(j, sc, bs);
+      if (!cfinite(s)) sc.count[1] = 1;
+    }
+  }
+}
+
+// s = r - alpha v
+template <int P>
+__global__ void __launch_bounds__(BX) k_bi_s(int Vh, int nrhs, const void* r, const void* v, void* sv, CgScal sc,
+                                             BiScal bs) {
+  typedef typename PT<P>::R R;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= Vh || !sc.active[j]) return;
+  const size_t sb = field_units_per_rhs(P, Vh) * 16 * j;
+  const double2 al = bs.alpha[j];
+  const R ar = (R)al.x, ai = (R)al.y;
+  const Spinor<R> rv = load_spinor<P>((const char*)r + sb, nullptr, Vh, i);
+  const Spinor<R> vv = load_spinor<P>((const char*)v + sb, nullptr, Vh, i);
+  Spinor<R> o;
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const Cx<R> x = vv.c[a][c];
+      o.c[a][c] = cx<R>(rv.c[a][c].re - (ar * x.re - ai * x.im), rv.c[a][c].im - (ar * x.im + ai * x.re));
+    }
+  store_spinor<P>((char*)sv + sb, nullptr, Vh, i, o);
+}
+
+// omega = (t, s) / (t, t) from the partials of sum conj(s) t and |t|^2
+__global__ void k_bi_omega(const double2* dpart, const double* npart, int nb, int nrhs, CgScal sc, BiScal bs) {
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (j >= nrhs || !sc.active[j]) return;
+  const int lane = threadIdx.x & 31;
+  double2 d = make_double2(0, 0);
+  double n = 0;
+  for (int b = lane; b < nb; b += 32) {
+    const double2 v = dpart[(size_t)j * nb + b];
+    d.x += v.x;
+    d.y += v.y;
+    n += npart[(size_t)j * nb + b];
+  }
+  d = warp_sum2(d);
+  n = warp_sum(n);
+  if (lane == 0) {
+    const double2 ts = make_double2(d.x, -d.y);     // (t, s) = conj(sum conj(s) t)
+    const double2 om = make_double2(ts.x / n, ts.y / n);
+    const bool ok = n > 0 && isfinite(n) && cfinite(om) && (om.x != 0.0 || om.y != 0.0);
+    bs.omega[j] = ok ? om : make_double2(0, 0);
+    if (!ok) {
+      bi_breakdown(j, sc, bs);
+      if (!isfinite(n)) sc.count[1] = 1;
+    }
+  }
+}
+
+// x += alpha p + omega s ; r = s - omega t ; partials of (r0, r) and |r|^2
+template <int P>
+__global__ void __launch_bounds__(BX) k_bi_xr(int Vh, int nrhs, void* x, void* r, const void* p, const void* sv,
+                                              const void* t, const void* r0, CgScal sc, BiScal bs, double2* cpart,
+                                              double* npart) {
+  typedef typename PT<P>::R R;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y;
+  const bool on = sc.active[j] != 0;
+  R dr = 0, di = 0, nn = 0;
+  if (i < Vh && on) {
+    const size_t sb = field_units_per_rhs(P, Vh) * 16 * j;
+    const double2 al = bs.alpha[j], om = bs.omega[j];
+    const R ar = (R)al.x, ai = (R)al.y, wr = (R)om.x, wi = (R)om.y;
+    Spinor<R> xv = load_spinor<P>((const char*)x + sb, nullptr, Vh, i);
+    const Spinor<R> pv = load_spinor<P>((const char*)p + sb, nullptr, Vh, i);
+    const Spinor<R> svv = load_spinor<P>((const char*)sv + sb, nullptr, Vh, i);
+    const Spinor<R> tv = load_spinor<P>((const char*)t + sb, nullptr, Vh, i);
+    const Spinor<R> zv = load_spinor<P>((const char*)r0 + sb, nullptr, Vh, i);
+    Spinor<R> rv;
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const Cx<R> pp = pv.c[a][c], ss = svv.c[a][c], tt = tv.c[a][c], z = zv.c[a][c];
+        xv.c[a][c].re += ar * pp.re - ai * pp.im + wr * ss.re - wi * ss.im;
+        xv.c[a][c].im += ar * pp.im + ai * pp.re + wr * ss.im + wi * ss.re;
+        const Cx<R> rr = cx<R>(ss.re - (wr * tt.re - wi * tt.im), ss.im - (wr * tt.im + wi * tt.re));
+        rv.c[a][c] = rr;
+        dr += z.re * rr.re + z.im * rr.im;
+        di += z.re * rr.im - z.im * rr.re;
+        nn += rr.re * rr.re + rr.im * rr.im;
+      }
+    store_spinor<P>((char*)x + sb, nullptr, Vh, i, xv);
+    store_spinor<P>((char*)r + sb, nullptr, Vh, i, rv);
+  }
+  __shared__ double red[3][BX / 32];
+  double vr = warp_sum((double)dr), vi = warp_sum((double)di), vn = warp_sum((double)nn);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = vr;
+    red[1][threadIdx.x >> 5] = vi;
+    red[2][threadIdx.x >> 5] = vn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && on) {
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int w = 0; w < BX / 32; w++) { a0 += red[0][w]; a1 += red[1][w]; a2 += red[2][w]; }
+    cpart[(size_t)j * gridDim.x + blockIdx.x] = make_double2(a0, a1);
+    npart[(size_t)j * gridDim.x + blockIdx.x] = a2;
+  }
+}
+
+// rho_new = (r0, r), |r|^2; beta = (rho_new / rho) (alpha / omega); reliable-update triggers
+__global__ void k_bi_beta(const double2* cpart, const double* npart, int nb, int nrhs, CgScal sc, BiScal bs,
+                          int max_since, double delta2) {
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (j >= nrhs || !sc.active[j]) return;
+  const int lane = threadIdx.x & 31;
+  double2 d = make_double2(0, 0);
+  double n = 0;
+  for (int b = lane; b < nb; b += 32) {
+    const double2 v = cpart[(size_t)j * nb + b];
+    d.x += v.x;
+    d.y += v.y;
+    n += npart[(size_t)j * nb + b];
+  }
+  d = warp_sum2(d);
+  n = warp_sum(n);
+  if (lane == 0) {
+    const double2 bt = cmul(cdiv(d, bs.rho[j]), cdiv(bs.alpha[j], bs.omega[j]));
+    const bool ok = cfinite(bt) && (d.x != 0.0 || d.y != 0.0);
+    bs.beta[j] = ok ? bt : make_double2(0, 0);
+    bs.rho[j] = d;
+    sc.rr[j] = n;
+    sc.iters[j] += 1;
+    sc.since[j] += 1;
+    if (!isfinite(n)) { sc.active[j] = 0; sc.count[1] = 1; }
+    else if (!ok) { sc.ru[j] = 1; bs.brk[j] = 1; }
+    else if (n <= sc.stop2[j] || sc.since[j] >= max_since || !(n > 0) || n * delta2 > 1e4 * sc.stop2[j])
+      sc.ru[j] = 1;                        // the pause takes effect after the p update (k_pause)
+  }
+}
+
+// p = r + beta (p - omega v)
+template <int P>
+__global__ void __launch_bounds__(BX) k_bi_p(int Vh, int nrhs, const void* r, void* p, const void* v, CgScal sc,
+                                             BiScal bs) {
+  typedef typename PT<P>::R R;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= Vh || !sc.active[j]) return;
+  const size_t sb = field_units_per_rhs(P, Vh) * 16 * j;
+  const double2 bt = bs.beta[j], om = bs.omega[j];
+  const R br = (R)bt.x, bi = (R)bt.y, wr = (R)om.x, wi = (R)om.y;
+  const Spinor<R> rv = load_spinor<P>((const char*)r + sb, nullptr, Vh, i);
+  const Spinor<R> vv = load_spinor<P>((const char*)v + sb, nullptr, Vh, i);
+  Spinor<R> pv = load_spinor<P>((const char*)p + sb, nullptr, Vh, i);
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const Cx<R> vx = vv.c[a][c];
+      const Cx<R> d = cx<R>(pv.c[a][c].re - (wr * vx.re - wi * vx.im), pv.c[a][c].im - (wr * vx.im + wi * vx.re));
+      pv.c[a][c] = cx<R>(rv.c[a][c].re + br * d.re - bi * d.im, rv.c[a][c].im + br * d.im + bi * d.re);
+    }
+  store_spinor<P>((char*)p + sb, nullptr, Vh, i, pv);
+}
+
+// partials of sum conj(a) b and |b|^2 per (rhs, block) for the rhs in mask
+template <int P>
+__global__ void __launch_bounds__(BX) k_dot_norm(int Vh, int nrhs, const void* a, const void* b, const int* mask,
+                                                 double2* cpart, double* npart) {
+  typedef typename PT<P>::R R;
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y;
+  const bool on = mask[j] != 0;
+  double dr = 0, di = 0, nn = 0;
+  if (i < Vh && on) {
+    const size_t sb = field_units_per_rhs(P, Vh) * 16 * j;
+    const Spinor<R> av = load_spinor<P>((const char*)a + sb, nullptr, Vh, i);
+    const Spinor<R> bv = load_spinor<P>((const char*)b + sb, nullptr, Vh, i);
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const Cx<R> x = av.c[s][c], y = bv.c[s][c];
+        dr += (double)x.re * y.re + (double)x.im * y.im;
+        di += (double)x.re * y.im - (double)x.im * y.re;
+        nn += (double)y.re * y.re + (double)y.im * y.im;
+      }
+  }
+  __shared__ double red[3][BX / 32];
+  dr = warp_sum(dr);
+  di = warp_sum(di);
+  nn = warp_sum(nn);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = dr;
+    red[1][threadIdx.x >> 5] = di;
+    red[2][threadIdx.x >> 5] = nn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && on) {
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int w = 0; w < BX / 32; w++) { a0 += red[0][w]; a1 += red[1][w]; a2 += red[2][w]; }
+    cpart[(size_t)j * gridDim.x + blockIdx.x] = make_double2(a0, a1);
+    npart[(size_t)j * gridDim.x + blockIdx.x] = a2;
+  }
+}
+
+// resume the updated rhs: rho = (r0, r), |r|^2 from the partials; restart flags consumed
+__global__ void k_bi_resume(const double2* cpart, const double* npart, int nb, int nrhs, CgScal sc, BiScal bs,
+                            double delta2) {
+  const int j = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (j >= nrhs || !sc.upd[j]) return;
+  const int lane = threadIdx.x & 31;
+  double2 d = make_double2(0, 0);
+  double n = 0;
+  for (int b = lane; b < nb; b += 32) {
+    const double2 v = cpart[(size_t)j * nb + b];
+    d.x += v.x;
+    d.y += v.y;
+    n += npart[(size_t)j * nb + b];
+  }
+  d = warp_sum2(d);
+  n = warp_sum(n);
+  if (lane == 0) {
+    sc.upd[j] = 0;
+    sc.ru[j] = 0;
+    sc.since[j] = 0;
+    bs.brk[j] = 0;
+    if (!(n > 0) || !isfinite(n) || !cfinite(d)) {
+      if (!isfinite(n)) sc.count[1] = 1;
+      sc.alive[j] = 0;
+      return;
+    }
+    bs.rho[j] = d;
+    sc.rr[j] = n;
+    sc.stop2[j] = delta2 * n;
+    sc.active[j] = 1;
+  }
+}
+
+// updated rhs that restart their shadow residual: the stagnating ones and those that broke down
+__global__ void k_bi_restart_mask(int nrhs, CgScal sc, BiScal bs, int first, int* rmask) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nrhs) return;
+  rmask[j] = sc.upd[j] && (first || sc.rst[j] || bs.brk[j]);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -309,6 +607,15 @@ struct SolveBufs {
   Field xl, rl, pl, ps, q, z, tmp, rhs;        // low precision (pl: vector precision, ps/q/z/tmp/rhs: stencil)
   double *part, *part2;
   CgScal sc;
+  // BiCGStab: v = Dhat p (q), s, t = Dhat s (z), shadow residual r0; complex partials
+  Field sl, r0;
+  double2 *cpart, *cpart2;
+  int* rmask;
+  BiScal bs;
+  // host copies of the set-up
+  std::vector<double> bn;
+  std::vector<int> alive0;
+  double* tmpd = nullptr;
 };
 
 static dlma_status rowsum(dlma_ctx* ctx, const double* part, int nb, int nrhs, double* out, int do_sqrt,
@@ -396,11 +703,12 @@ static dlma_status reliable_update(dlma_ctx* ctx, SolveBufs& B, int nrhs, double
   return DLMA_OK;
 }
 
+// Set-up shared by the solvers: buffers, per-rhs scalars, the even-odd source
+// bhat = b_e - D_eo T_oo^-1 b_o, |b| and s = |bhat| (the low-precision systems
+// solve for x / s), and the initial masks.
 template <int PB, int PS>
-static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol,
-                               dlma_solve_info* info, double delta, int max_inner, int max_since) {
+static dlma_status solve_setup(dlma_ctx* ctx, SolveBufs& B, const double* b_dev, int nrhs, bool bicg) {
   const int Vh = ctx->g.Vh;
-  SolveBufs B;
   TRY(field_alloc(ctx, WS_SOLVE_B, DLMA_FP64, 2 * nrhs, &B.b_e));
   B.b_o = B.b_e;
   B.b_e.nrhs = B.b_o.nrhs = nrhs;
@@ -421,9 +729,17 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   TRY(field_alloc(ctx, WS_CG_Z, PS, nrhs, &B.z));
   TRY(field_alloc(ctx, WS_CG_TMP, PS, nrhs, &B.tmp));
   TRY(field_alloc(ctx, WS_CG_RHS, PS, nrhs, &B.rhs));
+  if (bicg) {
+    TRY(field_alloc(ctx, WS_BI_S, PB, nrhs, &B.sl));
+    TRY(field_alloc(ctx, WS_BI_R0, PB, nrhs, &B.r0));
+  }
   const int nbmax = (Vh + 31) / 32 + 8;
   TRY(workT(ctx, WS_PART, (size_t)2 * nbmax * nrhs, &B.part));
   B.part2 = B.part + (size_t)nbmax * nrhs;
+  if (bicg) {
+    TRY(workT(ctx, WS_BI_PART, (size_t)2 * nbmax * nrhs, &B.cpart));
+    B.cpart2 = B.cpart + (size_t)nbmax * nrhs;
+  }
   double* sd;
   TRY(workT(ctx, WS_SCAL, (size_t)10 * nrhs + 64, &sd));
   B.sc.rr = sd;
@@ -434,10 +750,10 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   B.sc.bnorm = sd + 5 * nrhs;
   B.sc.scale = sd + 6 * nrhs;
   B.sc.rrnew = sd + 7 * nrhs;
-  double* tmpd = sd + 8 * nrhs;     // 2 nrhs scratch
+  B.tmpd = sd + 8 * nrhs;     // 2 nrhs scratch
   TRY(workT(ctx, WS_T0, (size_t)nrhs + 16, &B.sc.rbest));
   int* si;
-  TRY(workT(ctx, WS_ACT, (size_t)12 * nrhs + 16, &si));
+  TRY(workT(ctx, WS_ACT, (size_t)14 * nrhs + 16, &si));
   B.sc.active = si;
   B.sc.alive = si + nrhs;
   B.sc.ru = si + 2 * nrhs;
@@ -450,7 +766,16 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   B.sc.cf = si + 9 * nrhs;
   B.sc.exact = si + 10 * nrhs;
   B.sc.count = si + 11 * nrhs;
-  int* hcount = (int*)ctx->pinned;
+  B.bs.brk = si + 12 * nrhs;
+  B.rmask = si + 13 * nrhs;
+  if (bicg) {
+    double2* cs;
+    TRY(workT(ctx, WS_BI_SCAL, (size_t)4 * nrhs + 16, &cs));
+    B.bs.rho = cs;
+    B.bs.alpha = cs + nrhs;
+    B.bs.omega = cs + 2 * nrhs;
+    B.bs.beta = cs + 3 * nrhs;
+  }
 
   const dim3 gv((Vh + BX - 1) / BX, nrhs);
   TRY(pack_parity(ctx, b_dev, 1, 0, B.b_e));
@@ -459,11 +784,11 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   k_convert<DLMA_FP64, DLMA_FP64><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.b_e.data, nullptr, B.t64.data, nullptr,
                                                               nullptr, 0, nullptr, B.part);
   CHECK_LAUNCH();
-  TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd, 0, nullptr));
+  TRY(rowsum(ctx, B.part, gv.x, nrhs, B.tmpd, 0, nullptr));
   k_convert<DLMA_FP64, DLMA_FP64><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.b_o.data, nullptr, B.t64o.data, nullptr,
                                                               nullptr, 0, nullptr, B.part);
   CHECK_LAUNCH();
-  TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd + nrhs, 0, nullptr));
+  TRY(rowsum(ctx, B.part, gv.x, nrhs, B.tmpd + nrhs, 0, nullptr));
   // bhat = b_e - D_eo T_oo^-1 b_o and |bhat|
   {
     HopOp a;
@@ -478,43 +803,112 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   CHECK_LAUNCH();
   TRY(rowsum(ctx, B.part, gv.x, nrhs, B.sc.scale, 1, nullptr));
   std::vector<double> hb(2 * nrhs), hs(nrhs);
-  CU(cudaMemcpyAsync(hb.data(), tmpd, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(hb.data(), B.tmpd, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaMemcpyAsync(hs.data(), B.sc.scale, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
-  std::vector<double> bn(nrhs);
-  std::vector<int> alive0(nrhs), zeros(nrhs, 0);
+  B.bn.assign(nrhs, 0.0);
+  B.alive0.assign(nrhs, 0);
+  std::vector<int> zeros(nrhs, 0);
   for (int j = 0; j < nrhs; j++) {
-    bn[j] = sqrt(hb[j] + hb[nrhs + j]);
-    if (!isfinite(bn[j]) || !isfinite(hs[j])) return set_err(ctx, DLMA_ERR_NONFINITE, "a source holds NaN or Inf");
-    alive0[j] = bn[j] > 0 && hs[j] > 0;
+    B.bn[j] = sqrt(hb[j] + hb[nrhs + j]);
+    if (!isfinite(B.bn[j]) || !isfinite(hs[j])) return set_err(ctx, DLMA_ERR_NONFINITE, "a source holds NaN or Inf");
+    B.alive0[j] = B.bn[j] > 0 && hs[j] > 0;
   }
-  CU(cudaMemcpyAsync(B.sc.bnorm, bn.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
-  CU(cudaMemcpyAsync(B.sc.alive, alive0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
-  CU(cudaMemcpyAsync(B.sc.ru, alive0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemcpyAsync(B.sc.bnorm, B.bn.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemcpyAsync(B.sc.alive, B.alive0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemcpyAsync(B.sc.ru, B.alive0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
   for (int* z : {B.sc.active, B.sc.upd, B.sc.iters, B.sc.since, B.sc.nupd, B.sc.stall, B.sc.rst, B.sc.cf,
-                 B.sc.exact})
+                 B.sc.exact, B.bs.brk})
     CU(cudaMemcpyAsync(z, zeros.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
   std::vector<double> big(nrhs, 1e300);
   CU(cudaMemcpyAsync(B.sc.rbest, big.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
   CU(cudaMemsetAsync(B.sc.count, 0, 4 * sizeof(int), ctx->stream));
   CU(cudaMemsetAsync(B.x64.data, 0, field_bytes_per_rhs(DLMA_FP64, Vh) * nrhs, ctx->stream));
   CU(cudaMemsetAsync(B.xl.data, 0, field_bytes_per_rhs(PB, Vh) * nrhs, ctx->stream));
-  const double tol_target = 0.5 * tol;
-  const double delta2 = delta * delta;
+  // pack one full-batch right-hand side for the block-shape autotuner before any capture
+  k_convert<DLMA_FP64, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.bh.data, nullptr, B.rhs.data, B.rhs.scale,
+                                                       B.sc.scale, 1, nullptr, nullptr);
+  CHECK_LAUNCH();
+  TRY(autotune_hop(ctx, PS, B.rhs, B.tmp, B.z));
+  return DLMA_OK;
+}
+
+// x_o = T_oo^-1 (b_o - D_oe x_e), the full solution to x_dev, and the reported
+// residual of every right-hand side
+template <int PB>
+static dlma_status solve_finish(dlma_ctx* ctx, SolveBufs& B, double* x_dev, int nrhs, double tol,
+                                dlma_solve_info* info, dlma_status st) {
+  const int Vh = ctx->g.Vh;
+  const dim3 gv((Vh + BX - 1) / BX, nrhs);
+  // fold what is left of the low-precision solutions of unconverged rhs
+  if (st != DLMA_OK) {
+    k_fold<PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (double2*)B.x64.data, B.xl.data, B.sc.scale, B.sc.alive);
+    CHECK_LAUNCH();
+  }
+  {
+    HopOp r;
+    r.p_out = 1; r.own = 1; r.kout = 3; r.s = -1.0;
+    TRY(launch_hop(ctx, r, B.x64, &B.b_o, B.t64o));
+  }
+  TRY(unpack_parity(ctx, B.x64, 1, 0, x_dev));
+  TRY(unpack_parity(ctx, B.t64o, 1, 1, x_dev));
+  // reported residual ||b - D x|| / ||b||: for an rhs retired on an FP64 residual it is
+  // that residual, |bhat - Dhat x_e| (x_o above makes the odd rows of b - D x vanish);
+  // the rest (stopped early, or retired on a recursive residual) are evaluated on the
+  // full lattice in FP64 here
+  k_final_mask<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc);
+  CHECK_LAUNCH();
+  const int* fm = B.sc.cf;
+  Field xe = B.r64;
+  CU(cudaMemcpyAsync(xe.data, B.x64.data, field_bytes_per_rhs(DLMA_FP64, Vh) * nrhs, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  HopOp d;
+  d.own = 2; d.kout = 0; d.p_out = 0; d.active = fm;
+  TRY(launch_hop(ctx, d, B.t64o, &xe, B.t64));            // (Dx)_e
+  k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.b_e.data, (const double2*)B.t64.data,
+                                      (double2*)B.bh.data, fm, B.part);
+  CHECK_LAUNCH();
+  TRY(rowsum(ctx, B.part, gv.x, nrhs, B.tmpd, 0, fm));
+  d.p_out = 1;
+  TRY(launch_hop(ctx, d, xe, &B.t64o, B.t64));            // (Dx)_o
+  k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.b_o.data, (const double2*)B.t64.data,
+                                      (double2*)B.bh.data, fm, B.part);
+  CHECK_LAUNCH();
+  TRY(rowsum(ctx, B.part, gv.x, nrhs, B.tmpd + nrhs, 0, fm));
+  std::vector<double> h(2 * nrhs), hr(nrhs);
+  std::vector<int> hit(nrhs), hup(nrhs), hm(nrhs);
+  CU(cudaMemcpyAsync(h.data(), B.tmpd, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(hr.data(), B.sc.rnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(hm.data(), fm, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(hit.data(), B.sc.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(hup.data(), B.sc.nupd, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  bool all = true;
+  for (int j = 0; j < nrhs; j++) {
+    const double rn = hm[j] ? sqrt(h[j] + h[nrhs + j]) : (B.alive0[j] ? hr[j] : 0.0);
+    const double res = B.bn[j] > 0 ? rn / B.bn[j] : 0.0;
+    const int conv = res <= tol;
+    all = all && conv;
+    if (info) {
+      info[j].iters_inner = hit[j];
+      info[j].iters_outer = hup[j];
+      info[j].true_resid = res;
+      info[j].converged = conv;
+    }
+  }
+  if (st == DLMA_OK && !all) st = set_err(ctx, DLMA_ERR_NOT_CONVERGED, "true residual above tolerance");
+  return st;
+}
+
+// The chunked, graph-captured iteration loop shared by the solvers: `body` issues
+// one iteration, `update(first)` the reliable update of the paused rhs.
+template <class Body, class Update>
+static dlma_status iterate(dlma_ctx* ctx, SolveBufs& B, int nrhs, int max_inner, Body body, Update update) {
+  int* hcount = (int*)ctx->pinned;
   const int chunk = 8;
   const auto t_start = std::chrono::steady_clock::now();
   const double wall_limit_s = 600.0;
-
-  // the first "update" sets r_l = Dhat^dag (bhat / s) and p = r_l
-  {
-    // pack one full-batch right-hand side for the block-shape autotuner before any capture
-    k_convert<DLMA_FP64, PS><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.bh.data, nullptr, B.rhs.data, B.rhs.scale,
-                                                         B.sc.scale, 1, nullptr, nullptr);
-    CHECK_LAUNCH();
-    TRY(autotune_hop(ctx, PS, B.rhs, B.tmp, B.z));
-  }
-  TRY((reliable_update<PB, PS>(ctx, B, nrhs, tol_target, delta2, true)));
-
+  TRY(update(true));
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   uint64_t graph_kernels = 0;
@@ -525,14 +919,17 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
       const uint64_t l0 = ctx->launches;
       CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
       dlma_status cs = DLMA_OK;
-      for (int k = 0; k < chunk && cs == DLMA_OK; k++) cs = inner_iteration<PB, PS>(ctx, B, nrhs, max_since, delta2);
+      for (int k = 0; k < chunk && cs == DLMA_OK; k++) cs = body();
       if (cs == DLMA_OK) {
         k_count<<<1, 256, 0, ctx->stream>>>(B.sc.active, B.sc.ru, nrhs, B.sc.count);
         ctx->launches++;
       }
       const cudaError_t ce = cudaMemcpyAsync(hcount, B.sc.count, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
       const cudaError_t ee = cudaStreamEndCapture(ctx->stream, &graph);
-      if (cs != DLMA_OK) return cs;
+      if (cs != DLMA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return cs;
+      }
       if (ce != cudaSuccess || ee != cudaSuccess)
         return set_err(ctx, DLMA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ee != cudaSuccess ? ee : ce));
       CU(cudaGraphInstantiate(&gexec, graph, 0));
@@ -544,7 +941,10 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
     it += chunk;
     CU(cudaStreamSynchronize(ctx->stream));
     if (hcount[1]) { st = set_err(ctx, DLMA_ERR_NONFINITE, "non-finite value in the solve"); break; }
-    if (hcount[2] > 0) TRY((reliable_update<PB, PS>(ctx, B, nrhs, tol_target, delta2, false, PS == DLMA_FP16S)));
+    if (hcount[2] > 0) {
+      const dlma_status us = update(false);
+      if (us != DLMA_OK) { st = us; break; }
+    }
     k_count<<<1, 256, 0, ctx->stream>>>(B.sc.active, B.sc.ru, nrhs, B.sc.count);
     CHECK_LAUNCH();
     CU(cudaMemcpyAsync(hcount, B.sc.count, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -557,68 +957,157 @@ static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev
   }
   if (gexec) cudaGraphExecDestroy(gexec);
   if (graph) cudaGraphDestroy(graph);
-  if (st != DLMA_OK && st != DLMA_ERR_NOT_CONVERGED && st != DLMA_ERR_TIMEOUT) return st;
-  // fold what is left of the low-precision solutions of unconverged rhs
-  if (st != DLMA_OK) {
-    k_fold<PB><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (double2*)B.x64.data, B.xl.data, B.sc.scale, B.sc.alive);
-    CHECK_LAUNCH();
-  }
-  // x_o = T_oo^-1 (b_o - D_oe x_e)
-  {
-    HopOp r;
-    r.p_out = 1; r.own = 1; r.kout = 3; r.s = -1.0;
-    TRY(launch_hop(ctx, r, B.x64, &B.b_o, B.t64o));
-  }
-  TRY(unpack_parity(ctx, B.x64, 1, 0, x_dev));
-  TRY(unpack_parity(ctx, B.t64o, 1, 1, x_dev));
-  // reported residual ||b - D x|| / ||b||: for an rhs retired on an FP64 residual it is
-  // that residual, |bhat - Dhat x_e| (x_o above makes the odd rows of b - D x vanish);
-  // the rest (stopped early, or retired on a recursive residual) are evaluated on the
-  // full lattice in FP64 here
-  {
-    k_final_mask<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc);
-    CHECK_LAUNCH();
-    const int* fm = B.sc.cf;
-    Field xe = B.r64;
-    CU(cudaMemcpyAsync(xe.data, B.x64.data, field_bytes_per_rhs(DLMA_FP64, Vh) * nrhs, cudaMemcpyDeviceToDevice,
-                       ctx->stream));
-    HopOp d;
-    d.own = 2; d.kout = 0; d.p_out = 0; d.active = fm;
-    TRY(launch_hop(ctx, d, B.t64o, &xe, B.t64));            // (Dx)_e
-    k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.b_e.data, (const double2*)B.t64.data,
-                                        (double2*)B.bh.data, fm, B.part);
-    CHECK_LAUNCH();
-    TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd, 0, fm));
-    d.p_out = 1;
-    TRY(launch_hop(ctx, d, xe, &B.t64o, B.t64));            // (Dx)_o
-    k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.b_o.data, (const double2*)B.t64.data,
-                                        (double2*)B.bh.data, fm, B.part);
-    CHECK_LAUNCH();
-    TRY(rowsum(ctx, B.part, gv.x, nrhs, tmpd + nrhs, 0, fm));
-    std::vector<double> h(2 * nrhs), hr(nrhs);
-    std::vector<int> hit(nrhs), hup(nrhs), hm(nrhs);
-    CU(cudaMemcpyAsync(h.data(), tmpd, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(hr.data(), B.sc.rnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(hm.data(), fm, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(hit.data(), B.sc.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(hup.data(), B.sc.nupd, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    bool all = true;
-    for (int j = 0; j < nrhs; j++) {
-      const double rn = hm[j] ? sqrt(h[j] + h[nrhs + j]) : (alive0[j] ? hr[j] : 0.0);
-      const double res = bn[j] > 0 ? rn / bn[j] : 0.0;
-      const int conv = res <= tol;
-      all = all && conv;
-      if (info) {
-        info[j].iters_inner = hit[j];
-        info[j].iters_outer = hup[j];
-        info[j].true_resid = res;
-        info[j].converged = conv;
-      }
-    }
-    if (st == DLMA_OK && !all) st = set_err(ctx, DLMA_ERR_NOT_CONVERGED, "true residual above tolerance");
-  }
   return st;
+}
+
+template <int PB, int PS>
+static dlma_status solve_batch(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol,
+                               dlma_solve_info* info, double delta, int max_inner, int max_since) {
+  SolveBufs B;
+  TRY((solve_setup<PB, PS>(ctx, B, b_dev, nrhs, false)));
+  const double tol_target = 0.5 * tol;
+  const double delta2 = delta * delta;
+  // the first "update" sets r_l = Dhat^dag (bhat / s) and p = r_l
+  dlma_status st = iterate(
+      ctx, B, nrhs, max_inner, [&]() { return inner_iteration<PB, PS>(ctx, B, nrhs, max_since, delta2); },
+      [&](bool first) {
+        return reliable_update<PB, PS>(ctx, B, nrhs, tol_target, delta2, first, !first && PS == DLMA_FP16S);
+      });
+  if (st != DLMA_OK && st != DLMA_ERR_NOT_CONVERGED && st != DLMA_ERR_TIMEOUT) return st;
+  return solve_finish<PB>(ctx, B, x_dev, nrhs, tol, info, st);
+}
+
+// ---- BiCGStab on the Schur system, FP32 (or FP64) vectors and stencil ------
+// Per iteration: v = Dhat p with (r0, v); alpha = rho / (r0, v); s = r - alpha v;
+// t = Dhat s with (s, t) and |t|^2; omega = (t, s) / |t|^2; x += alpha p + omega s;
+// r = s - omega t with (r0, r) and |r|^2; beta = (rho' / rho)(alpha / omega);
+// p = r + beta (p - omega v).  Two operator applications per iteration, the inner
+// products in the stencil's and the vector kernels' epilogues.
+template <int P>
+static dlma_status bicg_iteration(dlma_ctx* ctx, SolveBufs& B, int nrhs, int max_since, double delta2) {
+  const int Vh = ctx->g.Vh;
+  const dim3 gv((Vh + BX - 1) / BX, nrhs);
+  const int nbh = hop_grid_x(ctx, P);
+  const int nw = (nrhs + 3) / 4;
+  // v = Dhat p (into q) with the partials of (r0, v)
+  TRY(schur_apply_dot(ctx, B.pl, B.tmp, B.q, B.sc.active, B.r0, B.cpart, nullptr));
+  k_bi_alpha<<<nw, 128, 0, ctx->stream>>>(B.cpart, nbh, nrhs, B.sc, B.bs);
+  CHECK_LAUNCH();
+  k_bi_s<P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, B.q.data, B.sl.data, B.sc, B.bs);
+  CHECK_LAUNCH();
+  // t = Dhat s (into z) with the partials of sum conj(s) t and |t|^2
+  TRY(schur_apply_dot(ctx, B.sl, B.tmp, B.z, B.sc.active, B.sl, B.cpart, B.part));
+  k_bi_omega<<<nw, 128, 0, ctx->stream>>>(B.cpart, B.part, nbh, nrhs, B.sc, B.bs);
+  CHECK_LAUNCH();
+  k_bi_xr<P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.xl.data, B.rl.data, B.pl.data, B.sl.data, B.z.data, B.r0.data,
+                                         B.sc, B.bs, B.cpart2, B.part2);
+  CHECK_LAUNCH();
+  k_bi_beta<<<nw, 128, 0, ctx->stream>>>(B.cpart2, B.part2, gv.x, nrhs, B.sc, B.bs, max_since, delta2);
+  CHECK_LAUNCH();
+  k_bi_p<P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, B.pl.data, B.q.data, B.sc, B.bs);
+  CHECK_LAUNCH();
+  k_pause<<<(nrhs + 127) / 128, 128, 0, ctx->stream>>>(nrhs, B.sc);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+// Reliable update of the paused rhs: x64 += s x_l, x_l = 0, r64 = bhat - Dhat x64 in
+// FP64; the converged retire; the rest continue with r_l = r64 / s and rho = (r0, r_l),
+// restarting r0 = p = r_l on the first update, after a breakdown or on stagnation.
+template <int P>
+static dlma_status bicg_update(dlma_ctx* ctx, SolveBufs& B, int nrhs, double tol_target, double delta2, bool first) {
+  const int Vh = ctx->g.Vh;
+  const dim3 gv((Vh + BX - 1) / BX, nrhs);
+  const int* ru = B.sc.ru;
+  const int nb1 = (nrhs + 127) / 128;
+  if (first) {
+    CU(cudaMemcpyAsync(B.r64.data, B.bh.data, field_bytes_per_rhs(DLMA_FP64, Vh) * nrhs, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    CU(cudaMemcpyAsync(B.sc.rnorm, B.sc.scale, sizeof(double) * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    k_fold<P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (double2*)B.x64.data, B.xl.data, B.sc.scale, ru);
+    CHECK_LAUNCH();
+    TRY(schur_apply(ctx, B.x64, B.t64o, B.t64, 0, ru, nullptr));
+    k_sub64<<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.bh.data, (const double2*)B.t64.data,
+                                        (double2*)B.r64.data, ru, B.part2);
+    CHECK_LAUNCH();
+    TRY(rowsum(ctx, B.part2, gv.x, nrhs, B.sc.rnorm, 1, ru));
+  }
+  k_mark_exact<<<nb1, 128, 0, ctx->stream>>>(nrhs, B.sc);
+  CHECK_LAUNCH();
+  k_ru_check<<<nb1, 128, 0, ctx->stream>>>(nrhs, B.sc, tol_target);
+  CHECK_LAUNCH();
+  const int* upd = B.sc.upd;
+  k_convert<DLMA_FP64, P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.r64.data, nullptr, B.rl.data, nullptr, B.sc.scale,
+                                                      1, upd, nullptr);
+  CHECK_LAUNCH();
+  k_bi_restart_mask<<<nb1, 128, 0, ctx->stream>>>(nrhs, B.sc, B.bs, first ? 1 : 0, B.rmask);
+  CHECK_LAUNCH();
+  k_convert<P, P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, nullptr, B.r0.data, nullptr, nullptr, 0, B.rmask,
+                                              nullptr);
+  CHECK_LAUNCH();
+  k_convert<P, P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, nullptr, B.pl.data, nullptr, nullptr, 0, B.rmask,
+                                              nullptr);
+  CHECK_LAUNCH();
+  k_dot_norm<P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.r0.data, B.rl.data, upd, B.cpart2, B.part2);
+  CHECK_LAUNCH();
+  k_bi_resume<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(B.cpart2, B.part2, gv.x, nrhs, B.sc, B.bs, delta2);
+  CHECK_LAUNCH();
+  return DLMA_OK;
+}
+
+template <int P>
+static dlma_status solve_batch_bicg(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol,
+                                    dlma_solve_info* info, double delta, int max_inner, int max_since) {
+  SolveBufs B;
+  TRY((solve_setup<P, P>(ctx, B, b_dev, nrhs, true)));
+  const double tol_target = 0.5 * tol;
+  const double delta2 = delta * delta;
+  dlma_status st = iterate(
+      ctx, B, nrhs, max_inner, [&]() { return bicg_iteration<P>(ctx, B, nrhs, max_since, delta2); },
+      [&](bool first) { return bicg_update<P>(ctx, B, nrhs, tol_target, delta2, first); });
+  if (st != DLMA_OK && st != DLMA_ERR_NOT_CONVERGED && st != DLMA_ERR_TIMEOUT) return st;
+  return solve_finish<P>(ctx, B, x_dev, nrhs, tol, info, st);
+}
+
+// One batch with the context's solver choice.  BiCGStab serves FP32 inner solves;
+// right-hand sides it leaves above the tolerance are solved again with CGNE.
+static dlma_status solve_one_batch(dlma_ctx* ctx, const double* b, double* x, int n, double tol, dlma_prec inner,
+                                   dlma_solve_info* inf) {
+  // delta: reduction of the iterated residual between FP64 reliable updates
+  if (inner == DLMA_FP64) return solve_batch<DLMA_FP64, DLMA_FP64>(ctx, b, x, n, tol, inf, 1e-6, 200000, 100000);
+  if (inner == DLMA_FP16S) return solve_batch<DLMA_FP32, DLMA_FP16S>(ctx, b, x, n, tol, inf, 3e-3, 40000, 400);
+  if (ctx->solver != DLMA_SOLVER_BICGSTAB)
+    return solve_batch<DLMA_FP32, DLMA_FP32>(ctx, b, x, n, tol, inf, 3e-4, 40000, 400);
+  std::vector<dlma_solve_info> li(n);
+  dlma_status s = solve_batch_bicg<DLMA_FP32>(ctx, b, x, n, tol, li.data(), 1e-3, 20000, 200);
+  if (s != DLMA_OK && s != DLMA_ERR_NOT_CONVERGED && s != DLMA_ERR_TIMEOUT) return s;
+  std::vector<int> bad;
+  for (int j = 0; j < n; j++)
+    if (!li[j].converged) bad.push_back(j);
+  if (!bad.empty()) {
+    // gather the unconverged sources, solve them with CGNE, scatter the solutions back
+    const size_t fb = (size_t)ctx->g.V * 24 * sizeof(double);
+    double *gb, *gx;
+    TRY(workT(ctx, WS_RETRY_B, bad.size() * fb / sizeof(double), &gb));
+    TRY(workT(ctx, WS_RETRY_X, bad.size() * fb / sizeof(double), &gx));
+    for (size_t q = 0; q < bad.size(); q++)
+      CU(cudaMemcpyAsync((char*)gb + q * fb, (const char*)b + bad[q] * fb, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+    std::vector<dlma_solve_info> ri(bad.size());
+    s = solve_batch<DLMA_FP32, DLMA_FP32>(ctx, gb, gx, (int)bad.size(), tol, ri.data(), 3e-4, 40000, 400);
+    if (s != DLMA_OK && s != DLMA_ERR_NOT_CONVERGED && s != DLMA_ERR_TIMEOUT) return s;
+    for (size_t q = 0; q < bad.size(); q++) {
+      CU(cudaMemcpyAsync((char*)x + bad[q] * fb, (const char*)gx + q * fb, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+      ri[q].iters_inner += li[bad[q]].iters_inner;
+      ri[q].iters_outer += li[bad[q]].iters_outer;
+      li[bad[q]] = ri[q];
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  bool all = true;
+  for (int j = 0; j < n; j++) all = all && li[j].converged;
+  if (inf) memcpy(inf, li.data(), sizeof(dlma_solve_info) * n);
+  return all ? DLMA_OK : set_err(ctx, DLMA_ERR_NOT_CONVERGED, "true residual above tolerance");
 }
 
 dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol, dlma_prec inner,
@@ -627,7 +1116,7 @@ dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int 
   const size_t Vh = ctx->g.Vh;
   size_t per_rhs = field_bytes_per_rhs(DLMA_FP64, Vh) * 7;
   const int pb = inner == DLMA_FP64 ? DLMA_FP64 : DLMA_FP32;
-  per_rhs += field_bytes_per_rhs(pb, Vh) * 3 + field_bytes_per_rhs(inner, Vh) * 5;
+  per_rhs += field_bytes_per_rhs(pb, Vh) * 5 + field_bytes_per_rhs(inner, Vh) * 5;
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
   size_t budget = (size_t)(0.85 * (double)(freeb + ctx->work_bytes));
@@ -640,11 +1129,7 @@ dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int 
     const double* b = b_dev + (size_t)j0 * ctx->g.V * 24;
     double* x = x_dev + (size_t)j0 * ctx->g.V * 24;
     dlma_solve_info* inf = info ? info + j0 : nullptr;
-    dlma_status s;
-    // delta: reduction of the iterated residual between FP64 reliable updates
-    if (inner == DLMA_FP64) s = solve_batch<DLMA_FP64, DLMA_FP64>(ctx, b, x, n, tol, inf, 1e-6, 200000, 100000);
-    else if (inner == DLMA_FP32) s = solve_batch<DLMA_FP32, DLMA_FP32>(ctx, b, x, n, tol, inf, 3e-4, 40000, 400);
-    else s = solve_batch<DLMA_FP32, DLMA_FP16S>(ctx, b, x, n, tol, inf, 3e-3, 40000, 400);
+    const dlma_status s = solve_one_batch(ctx, b, x, n, tol, inner, inf);
     if (s != DLMA_OK && s != DLMA_ERR_NOT_CONVERGED) return s;
     if (s != DLMA_OK) worst = s;
   }

@@ -5,6 +5,9 @@ synthetic gauge field for profiling, e.g.
         python -m paper_2201_09729_gb300.profile_stencil --prec fp32 --nrhs 32
 
 Prints the CUDA-event time of each application and the algorithmic bytes.
+With --sweep, every FP32 variant the autotuner chooses from (one or two
+right-hand sides per thread, 12- or 18-real links; each with its best block
+shape) is timed in a fresh context and reported.
 """
 import argparse
 import os
@@ -21,6 +24,7 @@ def main():
     ap.add_argument("--nrhs", type=int, default=32)
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--sweep", action="store_true")
     a = ap.parse_args()
     import torch
 
@@ -37,10 +41,25 @@ def main():
     Vh = a.L ** 3 * a.T // 2
     g = torch.Generator(device="cuda").manual_seed(1)
     v = torch.randn((a.nrhs, Vh, 4, 3), dtype=torch.complex128, device="cuda", generator=g)
+    by = schur_bytes(Vh, a.nrhs, a.prec)
+    if a.sweep:
+        ctx.close()
+        for nr, links in ((1, 12), (1, 18), (2, 12), (2, 18)):
+            os.environ["DLMA_FORCE_NR"], os.environ["DLMA_FORCE_LINKS"] = str(nr), str(links)
+            c = Context(a.L, a.T, 0, 0)
+            c.dlma_set_gauge(U)
+            c.dlma_set_params(1 / (2 * 0.1225) - 4, 1.0)
+            ms = []
+            for r in range(a.reps + 1):
+                c.dlma_apply_schur(v, 0, prec)
+                ms.append(c.dlma_last_timing()[0])
+            best = min(ms[1:])
+            print(f"nr {nr} links {links}: best {best:.3f} ms  {by / best / 1e6:.1f} GB/s algorithmic")
+            c.close()
+        return
     for r in range(a.reps):
         ctx.dlma_apply_schur(v, 0, prec)
         ms = ctx.dlma_last_timing()[0]
-        by = schur_bytes(Vh, a.nrhs, a.prec)
         print(f"rep {r}: {ms:.3f} ms  {by / ms / 1e6:.1f} GB/s algorithmic ({by / 1e6:.1f} MB)")
     ctx.close()
 

@@ -103,12 +103,13 @@ def test_solve_fp64_plain_workload_vs_lu(dl):
         assert _rel(x[j], xl[j]) < 1e-10
 
 
-@pytest.mark.parametrize("prec", ["FP32", "FP16S"])
-def test_mixed_precision_solve_ragged_batch(dl, prec):
+@pytest.mark.parametrize("prec,solver", [("FP32", "SOLVER_BICGSTAB"), ("FP32", "SOLVER_CGNE"), ("FP16S", "SOLVER_CGNE")])
+def test_mixed_precision_solve_ragged_batch(dl, prec, solver):
     # 7 right-hand sides (ragged against the 4-rhs block), one of them zero;
-    # V/2 = 432 sites: 6.75 tiles of 64
+    # V/2 = 432 sites: 6.75 tiles of 64; both Krylov methods of the FP32 solve
     L, T = 6, 4
     ctx, eo = _ctx(dl, L, T, 0.2, 0.0816, 1.0, 108)
+    ctx.dlma_set_solver(getattr(dl, solver))
     b = synth.gaussian_spinors(7, L ** 3 * T, 109)
     b[3] = 0
     x, info = ctx.dlma_solve(b, 1e-10, getattr(dl, prec))
@@ -131,8 +132,9 @@ def test_solve_precision_workload_residual_property(dl):
     ctx.dlma_set_params(wl.m0, wl.csw)
     eo = dirac.EvenOdd(U, wl.L, wl.T, wl.m0, wl.csw)
     b = synth.gaussian_spinors(2, wl.volume, 110)
-    for prec in (dl.FP32, dl.FP16S):
+    for prec, solver in ((dl.FP32, dl.SOLVER_BICGSTAB), (dl.FP32, dl.SOLVER_CGNE), (dl.FP16S, dl.SOLVER_CGNE)):
+        ctx.dlma_set_solver(solver)
         x, info = ctx.dlma_solve(b, 1e-10, prec)
         for j in range(2):
             r = np.linalg.norm((b[j] - eo.apply_full(x[j])).ravel()) / np.linalg.norm(b[j].ravel())
-            assert r <= 1e-10, (prec, j, r, info[j])
+            assert r <= 1e-10, (prec, solver, j, r, info[j])
