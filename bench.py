@@ -4,7 +4,7 @@
 One step = one pass of the whole hot path on the 16^3 x 32 precision workload
 (eps 0.2, kappa 0.1225, c_sw 1.0): the N = 32 lowest Laplacian modes of every
 timeslice, the 4N + 5 N_r = 168 sources of t' = 0 (N_r = 8 Z2 x Z2 noise
-vectors), their Wilson-clover solves to true residual 1e-10 (FP32 CGNE with
+vectors), their Wilson-clover solves to true residual 1e-10 (FP32 BiCGStab with
 FP64 reliable updates, all right-hand sides batched), the V^dag psi
 projections and the C_rest / C_mixed / C_dist contractions.
 
@@ -415,8 +415,8 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64" if args.inner == "fp32" else "f16+f32+f64", "data": "synthetic",
         "config": {"workload": f"{wl.name}: {wl.L}^3x{wl.T} lattice, eps {wl.eps}, kappa {wl.kappa}, c_sw {wl.csw}, "
                                f"N={N} Laplacian modes per timeslice, {4 * N} distillation + {5 * nn} noise solves "
-                               f"at t'={list(wl.t_src)}, true residual {wl.tol}, {args.inner} inner CGNE with FP64 "
-                               f"reliable updates",
+                               f"at t'={list(wl.t_src)}, true residual {wl.tol}, {args.inner} inner "
+                               f"{'BiCGStab' if args.inner == 'fp32' else 'CGNE'} with FP64 reliable updates",
                    "solves_per_step": J, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per-step working set > 10 GB)"},
         "e2e": {"value": whole_job_rate(J, world, e2e_ms), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
