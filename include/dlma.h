@@ -317,6 +317,28 @@ dlma_status dlma_correlators_plain(dlma_ctx* ctx, int t_src, int n_noise, const 
                                    double tol, dlma_prec inner, double* C, dlma_solve_info* info,
                                    dlma_mem mem);
 
+/* ---- conventional low-mode averaging with Dirac low modes (the control) ----
+ * Sec. 1 and the remark after Eq. 2: were Box built from eigenmodes of the
+ * Dirac operator, Box and the propagator would commute and C_mixed would
+ * vanish.  dlma_dirac_eigs: the N eigenpairs of the hermitian even-odd
+ * operator Qhat = g5 Dhat (even sites, Dhat the Schur complement of
+ * dlma_apply_schur) with the smallest |lambda|, in that order, found by
+ * Chebyshev-filtered subspace iteration on Qhat^2 = Dhat^dag Dhat in FP64 and a
+ * Rayleigh-Ritz of Qhat in the converged span.  evals [N] HOST (signed
+ * lambda); evecs complex [N][V/2][4][3] (even sites, lexicographic) in `mem`,
+ * may be NULL.  The modes are cached in the context until the gauge field or
+ * the parameters change.  Each pair meets ||Qhat u - lambda u|| <= tol
+ * max(1, |lambda|).  Errors: STATE, INVALID_ARG (N < 1, block N + max(8, N)
+ * above 510 or V/2 * 6), NOT_CONVERGED, CUDA. */
+dlma_status dlma_dirac_eigs(dlma_ctx* ctx, int N, double tol, double* evals, double* evecs, dlma_mem mem);
+
+/* dlma_dirac_project: out = P in (conj_g5 = 0) or g5 P g5 in (conj_g5 = 1) for
+ * even-site fields (complex [nrhs][V/2][4][3]), P = sum_i u_i u_i^dag over the
+ * cached Dirac low modes.  Since the even-even block of D^-1 is Dhat^-1 =
+ * Qhat^-1 g5, P Dhat^-1 (1 - g5 P g5) = 0: the mixed term of Eq. 2 with these
+ * modes vanishes.  Errors: STATE (no cached modes), INVALID_ARG, CUDA. */
+dlma_status dlma_dirac_project(dlma_ctx* ctx, const double* in, double* out, int nrhs, int conj_g5, dlma_mem mem);
+
 /* dlma_set_checkpoint: on != 0 makes dlma_correlators keep its forward
  * solutions (the 4N distillation solutions and phi_r, phibar_r of every noise
  * vector; the Krylov iterates are never kept) for dlma_correlators_backward;
@@ -370,6 +392,7 @@ uint64_t dlma_kernel_launches(const dlma_ctx* ctx);
  * the whole call for every call below; the others depend on the call:
  *   dlma_apply_schur          1 the two stencil launches, 2 their number (2)
  *   dlma_solve, _adjoint      -
+ *   dlma_dirac_eigs           1 subspace iterations
  *   dlma_laplacian_eigs       1 FP32 filter iterations, 2 FP64 iterations,
  *                             3 Laplacian applications (the matvec of Table 2),
  *                             4 orthogonalisation: Gram matrices, small

@@ -58,6 +58,8 @@ SIGNATURES = {
     "dlma_correlators_plain": (_ST, [_P, _I, _I, _P, _I, _D, _I, _P, _P, _I]),
     "dlma_solve_adjoint": (_ST, [_P, _P, _P, _I, _D, _I, _P, _I]),
     "dlma_real_dot": (_ST, [_P, _P, _P, C.c_uint64, _P, _I]),
+    "dlma_dirac_eigs": (_ST, [_P, _I, _D, _P, _P, _I]),
+    "dlma_dirac_project": (_ST, [_P, _P, _P, _I, _I, _I]),
     "dlma_set_checkpoint": (_ST, [_P, _I]),
     "dlma_checkpoint_serial": (C.c_uint64, [_P]),
     "dlma_correlators_backward": (_ST, [_P, _I, _I, _I, _P, _D, _I, _P, _P, _P, _I]),

@@ -277,6 +277,25 @@ class Context:
                                                     inner, _ptr(out), info, _mem(eta)))
         return {"C": out, "info": self._infos(info)}
 
+    def dlma_dirac_eigs(self, N: int, tol: float = 1e-10, device_out: bool = False):
+        """(lambda [N], u [N, V/2, 4, 3]) of Qhat = g5 Dhat with the smallest |lambda|."""
+        evals = np.empty(N, dtype=np.float64)
+        if device_out:
+            import torch
+            evecs = torch.empty((N, self.V // 2, 4, 3), dtype=torch.complex128, device="cuda")
+        else:
+            evecs = np.empty((N, self.V // 2, 4, 3), dtype=np.complex128)
+        self._check(self.lib.dlma_dirac_eigs(self.h, int(N), float(tol), _ptr(evals), _ptr(evecs), _mem(evecs)))
+        return evals, evecs
+
+    def dlma_dirac_project(self, v, conj_g5: bool = False):
+        """P v (or g5 P g5 v) over the cached Dirac low modes; v complex [n, V/2, 4, 3]."""
+        n = v.shape[0]
+        _check_c128(v, (n, self.V // 2, 4, 3), "v")
+        out = _empty_like(v, v.shape)
+        self._check(self.lib.dlma_dirac_project(self.h, _ptr(v), _ptr(out), n, int(bool(conj_g5)), _mem(v)))
+        return out
+
     def dlma_index_tables(self):
         eo = np.empty(self.V, dtype=np.int32)
         nbr = np.empty((2, 8, self.V // 2), dtype=np.int32)

@@ -136,6 +136,10 @@ struct dlma_ctx {
   std::vector<double> eig_lam;    // [T][N]
   std::vector<int> eig_have;      // [T] modes cached for timeslice t
 
+  // cached Dirac low modes (eigenvectors of g5 Dhat on the even sites), FP64 [N][12][V/2]
+  int dirac_N = 0;
+  double2* dirac_V = nullptr;
+
   // checkpointed forward solutions of dlma_correlators (for the backward):
   // [4N distillation, then phi_r, phibar_r per noise][V][4][3] complex
   int checkpoint = 0;
@@ -158,6 +162,7 @@ enum WorkSlot {
   WS_EIG_X, WS_EIG_Y, WS_EIG_Y2, WS_EIG_W, WS_EIG_G, WS_EIG_PART, WS_EIG_S, WS_EIG_AUX,
   WS_PROJ_V, WS_PROJ_PART, WS_PROJ_C, WS_CON, WS_CON2, WS_SRC, WS_SOL, WS_ETA,
   WS_BI_S, WS_BI_R0, WS_BI_PART, WS_BI_SCAL, WS_RETRY_B, WS_RETRY_X,
+  WS_TC_A, WS_TC_B, WS_TC_E,
   WS_COUNT
 };
 
@@ -272,6 +277,9 @@ dlma_status schur_dag_cgupdate(dlma_ctx* ctx, const Field& q, Field& tmp, const 
 void gamma_matrices(double G[4][4][4][2]);
 dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol,
                          dlma_prec inner, dlma_solve_info* info);
+// V^dag psi on the tensor cores, FP64-accurate (split-precision digits): coeff[j][Tsel][4][N]
+dlma_status project_tc(dlma_ctx* ctx, const double2* VT, int N, int Tsel, const double* psi, size_t stride_sites,
+                       int site_t0, int nrhs, double2* coeff);
 
 // per-context event timer helper
 struct EvTimer {

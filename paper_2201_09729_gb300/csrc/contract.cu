@@ -569,8 +569,12 @@ static dlma_status transpose_V(dlma_ctx* ctx, const double* V, int st_t, int st_
   return DLMA_OK;
 }
 
+// The projection runs on the tensor cores (tcproj.cu); DLMA_PROJECT_FP64=1 selects the
+// FP64 CUDA-core kernel k_project instead (the comparison path of the tests).
 static dlma_status project(dlma_ctx* ctx, const double2* VT, int N, int Tsel, const double* psi, size_t stride_sites,
                            int site_t0, int nrhs, double2* coeff) {
+  const char* sel = getenv("DLMA_PROJECT_FP64");
+  if (!(sel && atoi(sel) == 1)) return project_tc(ctx, VT, N, Tsel, psi, stride_sites, site_t0, nrhs, coeff);
   if (N > 256) return set_err(ctx, DLMA_ERR_INVALID_ARG, "N above 256 in the projection");
   const int nt = ((N + 31) / 32) * 32;
   // warps splitting the site sum: at most 4, partial sums within 40 KB of shared memory

@@ -391,6 +391,7 @@ static void free_all(dlma_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->ckpt) cudaFree(ctx->ckpt);
+  if (ctx->dirac_V) cudaFree(ctx->dirac_V);
   for (int i = 0; i < WS_COUNT; i++)
     if (ctx->wb[i].p) cudaFree(ctx->wb[i].p);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -532,6 +533,7 @@ extern "C" dlma_status dlma_set_gauge(dlma_ctx* ctx, const double* links, dlma_m
   CU(cudaStreamSynchronize(ctx->stream));
   ctx->have_params = false;
   ctx->eig_N = 0;
+  ctx->dirac_N = 0;
   ctx->gauge_gen++;
   if (h & 1) {
     ctx->have_gauge = false;
@@ -563,6 +565,7 @@ extern "C" dlma_status dlma_set_params(dlma_ctx* ctx, double m0, double c_sw) {
   ctx->m0 = m0;
   ctx->csw = c_sw;
   ctx->have_params = true;
+  ctx->dirac_N = 0;     // the Dirac low modes belong to the previous operator
   return DLMA_OK;
 }
 

@@ -137,3 +137,25 @@ def test_plain_estimator_vs_oracle(dl, prec, tol, ctol):
     want_d, _ = dilution.plain_diluted_correlators(lu, ew, wl.L, wl.T, tp)
     err = np.abs(rd["C"] - want_d).max(axis=1) / np.abs(want_d).max(axis=1)
     assert np.all(err <= ctol), err
+
+
+@pytest.mark.parametrize("L,T,N,nrhs", [(6, 4, 6, 5), (8, 4, 40, 37)])
+def test_tensor_core_projection_vs_fp64_and_oracle(dl, monkeypatch, L, T, N, nrhs):
+    # the split-precision tensor-core projection (default) and the FP64 CUDA-core
+    # kernel agree with the oracle to 1e-12 of the largest coefficient; magnitudes
+    # spread over five decades along the contraction, a mode count above one
+    # 32-mode block (N = 40) and a ragged row count (4 x 37 rows = 1.16 tiles of 128)
+    U = synth.gauge_field(L, T, 0.2, 311)
+    ctx = dl.Context(L, T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    V_all = np.stack([lap.lap_modes(lap.timeslice_links(U, L, t), L, N)[1] for t in range(T)])
+    psi = synth.gaussian_spinors(nrhs, L ** 3 * T, 312)
+    psi[:, ::7] *= 1e-5
+    got_tc = ctx.dlma_project(-1, np.ascontiguousarray(V_all), psi)
+    monkeypatch.setenv("DLMA_PROJECT_FP64", "1")
+    got_64 = ctx.dlma_project(-1, np.ascontiguousarray(V_all), psi)
+    for t in range(T):
+        w = np.transpose(dlma.coeffs(V_all[t], dlma.timeslice(psi, L, t)), (0, 2, 1))
+        scale = np.abs(w).max()
+        assert np.abs(got_tc[:, t] - w).max() <= 1e-12 * scale, (t, np.abs(got_tc[:, t] - w).max() / scale)
+        assert np.abs(got_64[:, t] - w).max() <= 1e-12 * scale

@@ -12,7 +12,9 @@ fixes independently of them (no GPU):
   (dense propagator) one;
 * the plain estimator (no distillation) is unbiased for the exact correlator,
   and with complete dilution it is exact; dropping its vector-channel solve is
-  caught.
+  caught;
+* with a projector on Dirac low modes (conventional LMA) the mixed propagator
+  block vanishes to rounding, with the Laplacian projector it does not.
 """
 import numpy as np
 import pytest
@@ -145,3 +147,48 @@ def test_plain_diluted_with_complete_dilution_is_exact():
     phi = np.transpose(S, (0, 2, 1, 3, 4, 5)).reshape(1, Vs * 3, 4, L ** 3 * T, 4, 3)
     got = dilution.plain_diluted(phi, L, T)
     assert np.abs(got - ex["full"]).max() < 1e-12 * np.abs(ex["full"]).max()
+
+
+def test_dirac_low_modes_make_the_mixed_block_vanish():
+    # Sec. 1 / after Eq. 2: with Box built from Dirac eigenmodes, Box and the propagator
+    # commute and C_mixed = 0.  Qhat = g5 Dhat is hermitian; P from its n smallest |lambda|
+    # gives P Dhat^-1 (1 - g5 P g5) = 0 to rounding, the Laplacian Box does not.
+    from oracle import lma
+    L, T = 2, 4
+    U = synth.gauge_field(L, T, 0.3, 78)
+    eo = dirac.EvenOdd(U, L, T, 1.0 / (2 * 0.12) - 4.0, 1.0)
+    Dh = lma.schur_matrix(eo)
+    # the dense Schur matrix is the oracle's own stencil
+    v = synth.gaussian_spinors(1, L ** 3 * T // 2, 79)[0]
+    assert np.abs(Dh @ v.ravel() - eo.schur(v).ravel()).max() < 1e-12
+    lam, u = lma.dirac_low_modes(eo, 6)
+    for i in range(6):
+        qu = dirac.apply_gamma5(eo.schur(u[i]))
+        assert np.linalg.norm(qu - lam[i] * u[i]) < 1e-11
+    Dinv = np.linalg.inv(Dh)
+    n = Dh.shape[0]
+    Uc = u.reshape(6, n).T
+    P = Uc @ np.conj(Uc.T)
+    G5 = lma.gamma5_matrix(n // 12)
+    mixed = P @ Dinv @ (np.eye(n) - G5 @ P @ G5)
+    assert np.abs(mixed).max() < 1e-12 * np.abs(Dinv).max()
+    # the Laplacian projector on the even sites of a timeslice does not commute
+    V_all = _modes(U, L, T, 2)
+    t = 1
+    even = eo.even
+    # Box restricted to the even sites of timeslice t, written out
+    Vt = V_all[t]
+    idx = [i for i, s in enumerate(even) if s // L ** 3 == t]
+    m_of = {i: even[i] % L ** 3 for i in idx}
+    Bx = np.zeros((n, n), dtype=np.complex128)
+    for i in idx:
+        for j in idx:
+            blk = np.einsum("kc,kd->cd", Vt[:, m_of[i], :], np.conj(Vt[:, m_of[j], :]))
+            for a in range(4):
+                Bx[12 * i + 3 * a:12 * i + 3 * a + 3, 12 * j + 3 * a:12 * j + 3 * a + 3] = blk
+    mixed_lap = Bx @ Dinv @ (np.eye(n) - Bx)
+    assert np.abs(mixed_lap).max() > 1e-3 * np.abs(Dinv).max()
+    # the projector helper of the oracle applies the same P (and g5 P g5)
+    w = synth.gaussian_spinors(1, n // 12, 80)[0]
+    assert np.abs(lma.project(u, w).ravel() - P @ w.ravel()).max() < 1e-13
+    assert np.abs(lma.project(u, w, True).ravel() - G5 @ P @ G5 @ w.ravel()).max() < 1e-13
