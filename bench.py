@@ -354,6 +354,7 @@ def main():
         dist.barrier()
     value = whole_job_rate(J, world, ms)
     iters = [i["iters_inner"] for i in res["info"]]
+    updates = [i["iters_outer"] for i in res["info"]]
 
     # e2e: the same step through HOST buffers, links / noise in, correlators out
     U_pin = torch.from_numpy(U_h).pin_memory()
@@ -438,6 +439,7 @@ def main():
                       "fp64_single_rhs_solves_per_s": fp64_sps,
                       "speedup_mixed_batched_vs_fp64_single": corr_solve_sps / fp64_sps,
                       "inner_iters_median": statistics.median(iters),
+                      "fp64_reliable_updates_median": statistics.median(updates),
                       "schur_ms": schur_ms},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == WORKLOAD:

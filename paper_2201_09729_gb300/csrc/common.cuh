@@ -98,6 +98,8 @@ struct dlma_ctx {
   int hop_sx[3] = {64, 64, 64}, hop_sy[3] = {4, 4, 4}, hop_tuned[3] = {0, 0, 0};
   int hop_l18[3] = {0, 0, 0};   // FP32: read 18-real links instead of rebuilding row 2
   int hop_nr[3] = {1, 1, 1};    // FP32: right-hand sides per thread (1 or 2)
+  // solve batch size per precision, chosen by autotune_batch (valid up to batch_tuned_nb)
+  int batch_rhs[3] = {0, 0, 0}, batch_tuned_nb[3] = {0, 0, 0}, batch_tuned[3] = {0, 0, 0};
 
   bool have_gauge = false, have_params = false;
   double m0 = 0, csw = 0;

@@ -18,6 +18,7 @@
 // never waits without bound.
 #include "fieldio.cuh"
 #include <chrono>
+#include <thread>
 #include <math.h>
 
 namespace {
@@ -104,6 +105,31 @@ __global__ void k_cg_beta(const double* part, int nb, int nrhs, CgScal sc, int m
 __global__ void k_pause(int nrhs, CgScal sc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < nrhs && sc.ru[j]) sc.active[j] = 0;
+}
+
+// End of one pass of the persistent solve loop: count the iterating rhs and decide,
+// on the device, whether the WHILE node of the solve graph runs another pass.  It
+// stops when no rhs iterates, on a non-finite value, after max_chunks passes
+// (count[3] = 1) or when the host has raised the stop flag (count[3] = 2).
+__global__ void k_loop(cudaGraphConditionalHandle h, const int* act, const int* ru, int n, int* count, int max_chunks,
+                       const volatile int* stop) {
+  __shared__ int s0, s2;
+  if (threadIdx.x == 0) { s0 = 0; s2 = 0; }
+  __syncthreads();
+  int c0 = 0, c2 = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) { c0 += act[j] != 0; c2 += ru[j] != 0; }
+  atomicAdd(&s0, c0);
+  atomicAdd(&s2, c2);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    count[0] = s0;
+    count[2] = s2;
+    const int chunks = ++count[4];
+    const bool halt = *stop != 0;
+    const bool go = (s0 > 0 || s2 > 0) && !count[1] && chunks < max_chunks && !halt;
+    if (!go && (s0 > 0 || s2 > 0)) count[3] = halt ? 2 : (count[1] ? 0 : 1);
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+  }
 }
 
 // count[0] = iterating rhs, count[2] = rhs paused for an update
@@ -753,7 +779,7 @@ static dlma_status solve_setup(dlma_ctx* ctx, SolveBufs& B, const double* b_dev,
   B.tmpd = sd + 8 * nrhs;     // 2 nrhs scratch
   TRY(workT(ctx, WS_T0, (size_t)nrhs + 16, &B.sc.rbest));
   int* si;
-  TRY(workT(ctx, WS_ACT, (size_t)14 * nrhs + 16, &si));
+  TRY(workT(ctx, WS_ACT, (size_t)14 * nrhs + 32, &si));
   B.sc.active = si;
   B.sc.alive = si + nrhs;
   B.sc.ru = si + 2 * nrhs;
@@ -765,7 +791,7 @@ static dlma_status solve_setup(dlma_ctx* ctx, SolveBufs& B, const double* b_dev,
   B.sc.rst = si + 8 * nrhs;
   B.sc.cf = si + 9 * nrhs;
   B.sc.exact = si + 10 * nrhs;
-  B.sc.count = si + 11 * nrhs;
+  B.sc.count = si + 14 * nrhs;     // [0] iterating, [1] non-finite, [2] paused, [3] stop reason, [4] passes
   B.bs.brk = si + 12 * nrhs;
   B.rmask = si + 13 * nrhs;
   if (bicg) {
@@ -900,64 +926,90 @@ static dlma_status solve_finish(dlma_ctx* ctx, SolveBufs& B, double* x_dev, int 
   return st;
 }
 
-// The chunked, graph-captured iteration loop shared by the solvers: `body` issues
-// one iteration, `update(first)` the reliable update of the paused rhs.
+// The persistent iteration loop shared by the solvers.  After the first reliable
+// update (`update(true)`), one CUDA graph runs the whole solve: a WHILE
+// conditional node whose body is `chunk` iterations (`body`), the reliable
+// update of the rhs paused in them (`update(false)`: every kernel of it is masked
+// by the paused / updated rhs, so a pass without pauses costs only empty
+// launches) and k_loop, which decides on the device whether to run another pass.
+// The host launches the graph once and waits by polling with a wall-clock
+// limit; at the limit it raises a stop flag in pinned memory that k_loop reads,
+// so the graph ends after the pass in flight and no wait is unbounded.
 template <class Body, class Update>
 static dlma_status iterate(dlma_ctx* ctx, SolveBufs& B, int nrhs, int max_inner, Body body, Update update) {
+  volatile int* hpin = (volatile int*)ctx->pinned;   // [0..7] counts (copied back), [16] stop flag
   int* hcount = (int*)ctx->pinned;
   const int chunk = 8;
-  const auto t_start = std::chrono::steady_clock::now();
   const double wall_limit_s = 600.0;
   TRY(update(true));
-  cudaGraphExec_t gexec = nullptr;
+  CU(cudaMemsetAsync(B.sc.count, 0, 8 * sizeof(int), ctx->stream));
+  hpin[16] = 0;
   cudaGraph_t graph = nullptr;
-  uint64_t graph_kernels = 0;
-  dlma_status st = DLMA_OK;
-  int it = 0;
-  while (true) {
-    if (!gexec) {
-      const uint64_t l0 = ctx->launches;
-      CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      dlma_status cs = DLMA_OK;
-      for (int k = 0; k < chunk && cs == DLMA_OK; k++) cs = body();
-      if (cs == DLMA_OK) {
-        k_count<<<1, 256, 0, ctx->stream>>>(B.sc.active, B.sc.ru, nrhs, B.sc.count);
-        ctx->launches++;
-      }
-      const cudaError_t ce = cudaMemcpyAsync(hcount, B.sc.count, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-      const cudaError_t ee = cudaStreamEndCapture(ctx->stream, &graph);
-      if (cs != DLMA_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return cs;
-      }
-      if (ce != cudaSuccess || ee != cudaSuccess)
-        return set_err(ctx, DLMA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ee != cudaSuccess ? ee : ce));
-      CU(cudaGraphInstantiate(&gexec, graph, 0));
-      graph_kernels = ctx->launches - l0;
-      ctx->launches = l0;
-    }
-    CU(cudaGraphLaunch(gexec, ctx->stream));
-    ctx->launches += graph_kernels;
-    it += chunk;
-    CU(cudaStreamSynchronize(ctx->stream));
-    if (hcount[1]) { st = set_err(ctx, DLMA_ERR_NONFINITE, "non-finite value in the solve"); break; }
-    if (hcount[2] > 0) {
-      const dlma_status us = update(false);
-      if (us != DLMA_OK) { st = us; break; }
-    }
-    k_count<<<1, 256, 0, ctx->stream>>>(B.sc.active, B.sc.ru, nrhs, B.sc.count);
-    CHECK_LAUNCH();
-    CU(cudaMemcpyAsync(hcount, B.sc.count, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
-    if (hcount[1]) { st = set_err(ctx, DLMA_ERR_NONFINITE, "non-finite value in the solve"); break; }
-    if (hcount[0] == 0 && hcount[2] == 0) break;
-    if (it >= max_inner) { st = set_err(ctx, DLMA_ERR_NOT_CONVERGED, "iteration cap %d reached", max_inner); break; }
-    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-    if (el > wall_limit_s) { st = set_err(ctx, DLMA_ERR_TIMEOUT, "solve exceeded %.0f s", wall_limit_s); break; }
+  cudaGraphExec_t gexec = nullptr;
+  CU(cudaGraphCreate(&graph, 0));
+  auto fail = [&](dlma_status s) {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  };
+  cudaGraphConditionalHandle handle;
+  cudaError_t ce = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+  if (ce != cudaSuccess) return fail(set_err(ctx, DLMA_ERR_CUDA, "conditional handle: %s", cudaGetErrorString(ce)));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  ce = cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp);
+  if (ce != cudaSuccess) return fail(set_err(ctx, DLMA_ERR_CUDA, "WHILE node: %s", cudaGetErrorString(ce)));
+  cudaGraph_t loop_body = cp.conditional.phGraph_out[0];
+  const uint64_t l0 = ctx->launches;
+  ce = cudaStreamBeginCaptureToGraph(ctx->stream, loop_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (ce != cudaSuccess) return fail(set_err(ctx, DLMA_ERR_CUDA, "capture: %s", cudaGetErrorString(ce)));
+  dlma_status cs = DLMA_OK;
+  for (int k = 0; k < chunk && cs == DLMA_OK; k++) cs = body();
+  if (cs == DLMA_OK) cs = update(false);
+  if (cs == DLMA_OK) {
+    k_loop<<<1, 256, 0, ctx->stream>>>(handle, B.sc.active, B.sc.ru, nrhs, B.sc.count,
+                                       std::max(1, max_inner / chunk), (const volatile int*)(hpin + 16));
+    ctx->launches++;
   }
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (graph) cudaGraphDestroy(graph);
-  return st;
+  cudaGraph_t captured = nullptr;
+  ce = cudaStreamEndCapture(ctx->stream, &captured);
+  if (cs != DLMA_OK) return fail(cs);
+  if (ce != cudaSuccess) return fail(set_err(ctx, DLMA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce)));
+  const uint64_t body_kernels = ctx->launches - l0;
+  ctx->launches = l0;
+  ce = cudaGraphInstantiate(&gexec, graph, 0);
+  if (ce != cudaSuccess) return fail(set_err(ctx, DLMA_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce)));
+  ce = cudaGraphLaunch(gexec, ctx->stream);
+  if (ce != cudaSuccess) return fail(set_err(ctx, DLMA_ERR_CUDA, "graph launch: %s", cudaGetErrorString(ce)));
+  // bounded wait: poll; at the wall-clock limit ask the device loop to stop
+  const auto t_start = std::chrono::steady_clock::now();
+  bool stopped = false;
+  while (true) {
+    const cudaError_t q = cudaStreamQuery(ctx->stream);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return fail(set_err(ctx, DLMA_ERR_CUDA, "solve graph: %s", cudaGetErrorString(q)));
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (!stopped && el > wall_limit_s) {
+      hpin[16] = 1;
+      stopped = true;
+    }
+    if (stopped && el > 2 * wall_limit_s)
+      return fail(set_err(ctx, DLMA_ERR_TIMEOUT, "solve graph did not stop after the wall-clock limit"));
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  CU(cudaMemcpyAsync(hcount, B.sc.count, 8 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->launches += body_kernels * (uint64_t)std::max(0, hcount[4]);
+  cudaGraphExecDestroy(gexec);
+  cudaGraphDestroy(graph);
+  if (hcount[1]) return set_err(ctx, DLMA_ERR_NONFINITE, "non-finite value in the solve");
+  if (hcount[3] == 2) return set_err(ctx, DLMA_ERR_TIMEOUT, "solve exceeded %.0f s", wall_limit_s);
+  if (hcount[3] == 1) return set_err(ctx, DLMA_ERR_NOT_CONVERGED, "iteration cap %d reached", max_inner);
+  return DLMA_OK;
 }
 
 template <int PB, int PS>
@@ -1080,7 +1132,10 @@ static dlma_status solve_one_batch(dlma_ctx* ctx, const double* b, double* x, in
   if (ctx->solver != DLMA_SOLVER_BICGSTAB)
     return solve_batch<DLMA_FP32, DLMA_FP32>(ctx, b, x, n, tol, inf, 3e-4, 40000, 400);
   std::vector<dlma_solve_info> li(n);
-  dlma_status s = solve_batch_bicg<DLMA_FP32>(ctx, b, x, n, tol, li.data(), 1e-3, 20000, 200);
+  // the reduction of |r| between FP64 updates (DLMA_BICG_DELTA overrides it for tuning)
+  double delta = 1e-3;
+  if (const char* e = getenv("DLMA_BICG_DELTA")) delta = std::min(0.5, std::max(1e-8, atof(e)));
+  dlma_status s = solve_batch_bicg<DLMA_FP32>(ctx, b, x, n, tol, li.data(), delta, 20000, 200);
   if (s != DLMA_OK && s != DLMA_ERR_NOT_CONVERGED && s != DLMA_ERR_TIMEOUT) return s;
   std::vector<int> bad;
   for (int j = 0; j < n; j++)
@@ -1110,6 +1165,53 @@ static dlma_status solve_one_batch(dlma_ctx* ctx, const double* b, double* x, in
   return all ? DLMA_OK : set_err(ctx, DLMA_ERR_NOT_CONVERGED, "true residual above tolerance");
 }
 
+// Batch-size autotuner: the stencil's time per right-hand side at the largest
+// batch memory allows (nb) and at nb / 2, nb / 4, measured once per precision on
+// the context's own lattice (the choice is kept until a larger batch fits); the
+// solves then run in batches of the cheapest size.  Links and clover are shared
+// by every right-hand side of a batch, so larger batches usually win; the
+// measurement decides where L2 reuse or occupancy says otherwise.
+static dlma_status autotune_batch(dlma_ctx* ctx, dlma_prec prec, int nb, int* out) {
+  if (ctx->batch_tuned[prec] && nb <= ctx->batch_tuned_nb[prec]) {
+    *out = std::min(nb, ctx->batch_rhs[prec]);
+    return DLMA_OK;
+  }
+  Field in, tmp, res;
+  TRY(field_alloc(ctx, WS_CG_RHS, prec, nb, &in));
+  TRY(field_alloc(ctx, WS_CG_TMP, prec, nb, &tmp));
+  TRY(field_alloc(ctx, WS_CG_Z, prec, nb, &res));
+  CU(cudaMemsetAsync(in.data, 0, field_bytes_per_rhs(prec, ctx->g.Vh) * nb, ctx->stream));
+  TRY(autotune_hop(ctx, prec, in, tmp, res));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  int best_k = nb;
+  double best = 1e300;
+  for (int k : {nb, (nb + 1) / 2, (nb + 3) / 4}) {
+    Field a = in, t = tmp, r = res;
+    a.nrhs = t.nrhs = r.nrhs = k;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3; rep++) {
+      CU(cudaEventRecord(e0, ctx->stream));
+      TRY(schur_apply(ctx, a, t, r, 0, nullptr, nullptr));
+      CU(cudaEventRecord(e1, ctx->stream));
+      CU(cudaEventSynchronize(e1));
+      float ms = 0;
+      CU(cudaEventElapsedTime(&ms, e0, e1));
+      tmin = std::min(tmin, ms);
+    }
+    const double per = tmin / k;
+    if (per < 0.97 * best) { best = per; best_k = k; }    // a smaller batch must win clearly
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->batch_rhs[prec] = best_k;
+  ctx->batch_tuned_nb[prec] = nb;
+  ctx->batch_tuned[prec] = 1;
+  *out = std::min(nb, best_k);
+  return DLMA_OK;
+}
+
 dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int nrhs, double tol, dlma_prec inner,
                          dlma_solve_info* info) {
   // batch size bounded by the memory cap (or 85% of free memory)
@@ -1121,8 +1223,9 @@ dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int 
   cudaMemGetInfo(&freeb, &totb);
   size_t budget = (size_t)(0.85 * (double)(freeb + ctx->work_bytes));
   if (ctx->memcap) budget = ctx->memcap;
-  const int nb = (int)std::min<size_t>((size_t)nrhs, budget / per_rhs);
+  int nb = (int)std::min<size_t>((size_t)nrhs, budget / per_rhs);
   if (nb < 1) return set_err(ctx, DLMA_ERR_OOM, "one right-hand side needs %zu bytes", per_rhs);
+  if (inner != DLMA_FP64 && nb > 16) TRY(autotune_batch(ctx, inner, nb, &nb));
   dlma_status worst = DLMA_OK;
   for (int j0 = 0; j0 < nrhs; j0 += nb) {
     const int n = std::min(nb, nrhs - j0);
