@@ -458,7 +458,9 @@ template <class R> static dlma_status rotate(Eig& E, const Cx<R>* X, Cx<R>* Z) {
   return DLMA_OK;
 }
 
-// small Rayleigh-Ritz problems in precision T (float in phase A, double in phase B)
+// small Rayleigh-Ritz problems in precision T (float in phase A, double in phase B,
+// where the column-scaled block has a well-conditioned Gram matrix and the
+// orthonormalisation takes the Cholesky route)
 template <class T> static dlma_status small_rr(Eig& E) {
   dlma_ctx* ctx = E.ctx;
   const size_t sm = (size_t)3 * E.m * (E.m + 1) * sizeof(Cx<T>);   // three m x (m + 1) work matrices
@@ -467,8 +469,9 @@ template <class T> static dlma_status small_rr(Eig& E) {
   phase(E, kPhOrtho);
   if (use_smem) CU(cudaFuncSetAttribute(k_small_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   CU(cudaMemsetAsync(E.dropped, 0, sizeof(int), ctx->stream));
+  const int chol = sizeof(T) == 8 ? 1 : 0;
   k_small_rr<T><<<E.Tn, 256, use_smem ? sm : 0, ctx->stream>>>(E.G, E.H, E.m, E.C, E.theta, (Cx<T>*)E.gwork,
-                                                               use_smem, E.dropped, E.drop_rel);
+                                                               use_smem, E.dropped, E.drop_rel, chol);
   CHECK_LAUNCH();
   return DLMA_OK;
 }

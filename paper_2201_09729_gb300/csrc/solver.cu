@@ -1133,7 +1133,7 @@ static dlma_status solve_one_batch(dlma_ctx* ctx, const double* b, double* x, in
     return solve_batch<DLMA_FP32, DLMA_FP32>(ctx, b, x, n, tol, inf, 3e-4, 40000, 400);
   std::vector<dlma_solve_info> li(n);
   // the reduction of |r| between FP64 updates (DLMA_BICG_DELTA overrides it for tuning)
-  double delta = 1e-3;
+  double delta = 3e-4;
   if (const char* e = getenv("DLMA_BICG_DELTA")) delta = std::min(0.5, std::max(1e-8, atof(e)));
   dlma_status s = solve_batch_bicg<DLMA_FP32>(ctx, b, x, n, tol, li.data(), delta, 20000, 200);
   if (s != DLMA_OK && s != DLMA_ERR_NOT_CONVERGED && s != DLMA_ERR_TIMEOUT) return s;
