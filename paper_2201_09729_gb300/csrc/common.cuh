@@ -98,6 +98,13 @@ struct dlma_ctx {
   int hop_sx[3] = {64, 64, 64}, hop_sy[3] = {4, 4, 4}, hop_tuned[3] = {0, 0, 0};
   int hop_l18[3] = {0, 0, 0};   // FP32: read 18-real links instead of rebuilding row 2
   int hop_nr[3] = {1, 1, 1};    // FP32: right-hand sides per thread (1 or 2)
+  // the Laplacian eigensolver's FP64 phase computes its Gram matrices and rotations
+  // in double-float (dfloat.cuh) for tol >= 1e-11; DLMA_DF_EIGS=0 at context
+  // creation keeps FP64 arithmetic
+  int df_eigs = 1;
+  // solves run as one persistent CUDA graph per batch (DLMA_SOLVE_GRAPH=0 at
+  // context creation launches the same passes from the host)
+  int solve_graph = 1;
   // solve batch size per precision, chosen by autotune_batch (valid up to batch_tuned_nb)
   int batch_rhs[3] = {0, 0, 0}, batch_tuned_nb[3] = {0, 0, 0}, batch_tuned[3] = {0, 0, 0};
 

@@ -21,12 +21,15 @@
 // so the FP32 rounding only touches the (small) E, and Y = X + E_d / s_d (the
 // filtered block with every column divided by its own s_d, so that the Gram
 // matrix stays well conditioned) is formed in FP64.  Stops when every wanted
-// pair has ||A x - theta x|| <= tol max(theta, 1).
+// pair has ||A x - theta x|| <= tol max(theta, 1).  For tol >= 1e-11 the FP64
+// blocks' Gram matrices and rotations compute in double-float (~46 bits,
+// dfloat.cuh) on the FP32 units; the matvec and the small problems stay FP64.
 //
 // Block layout (row-major per timeslice): element (t, row r = 3 site + colour,
 // column j) of a batch of Tn timeslices at (t * 3 Vs + r) * m + j, so a warp
 // reads consecutive columns of one site (coalesced) and shares its links.
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "smalleig.cuh"
 #include <algorithm>
 #include <math.h>
@@ -56,9 +59,44 @@ __device__ __forceinline__ void load_link3(const float4* __restrict__ U, int k, 
   u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
 }
 
+// NC adjacent complex entries starting at p (16-byte aligned when NC is even): FP32
+// pairs move as one 128-bit access
+template <int NC>
+__device__ __forceinline__ void ld_cols(const Cx<float>* __restrict__ p, Cx<float> (&v)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; c += 2) {
+    const float4 e = *(const float4*)(p + c);
+    v[c] = cx<float>(e.x, e.y);
+    v[c + 1] = cx<float>(e.z, e.w);
+  }
+}
+template <int NC>
+__device__ __forceinline__ void ld_cols(const Cx<double>* __restrict__ p, Cx<double> (&v)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; c++) v[c] = p[c];
+}
+template <int NC>
+__device__ __forceinline__ void st_cols(Cx<float>* p, const Cx<float> (&v)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; c += 2) *(float4*)(p + c) = make_float4(v[c].re, v[c].im, v[c + 1].re, v[c + 1].im);
+}
+template <int NC>
+__device__ __forceinline__ void st_cols(Cx<double>* p, const Cx<double> (&v)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; c++) p[c] = v[c];
+}
+
+// storage (R) <-> arithmetic (A) precision: A = R, or A = df for FP64 storage (the
+// double-float arithmetic of the FP64 phase, see dfloat.cuh)
+template <class A, class R> __device__ __forceinline__ Cx<A> to_a(Cx<R> v) { return cx<A>((A)v.re, (A)v.im); }
+template <class R, class A> __device__ __forceinline__ Cx<R> to_s(Cx<A> v) { return cx<R>((R)v.re, (R)v.im); }
+
 // out = alpha_t (A in) + beta_t in + gamma_t prev + alpha_t s[t][j] rin,  A = 6 - hopping = -lap
-// (in == nullptr: the stencil and beta terms vanish; prev / rin may be nullptr)
-template <class R>
+// (in == nullptr: the stencil and beta terms vanish; prev / rin may be nullptr).
+// One thread per (site, NC adjacent columns): the six links of the site are loaded
+// (and, in FP32, rebuilt from 12 reals) once for NC columns.  The block is
+// [t][site][colour][m] with m even, so a pair of FP32 columns is 16-byte aligned.
+template <class R, class A, int NC>
 __global__ void __launch_bounds__(256) k_lap(Geom g, int t0, int Tn, int m, const typename LinkT<R>::T* __restrict__ U,
                                              const Cx<R>* __restrict__ in, const Cx<R>* __restrict__ prev,
                                              const Cx<float>* __restrict__ rin, const double* __restrict__ scol,
@@ -66,25 +104,33 @@ __global__ void __launch_bounds__(256) k_lap(Geom g, int t0, int Tn, int m, cons
   // 32-bit index arithmetic (the host keeps Tn Vs m below 2^31): 64-bit divisions
   // would cost more than the stencil's arithmetic
   const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned total = (unsigned)Tn * (unsigned)g.Vs * (unsigned)m;
+  const unsigned mg = (unsigned)m / NC;
+  const unsigned total = (unsigned)Tn * (unsigned)g.Vs * mg;
   if (e >= total) return;
-  const unsigned sl = e / (unsigned)m;
-  const int j = (int)(e - sl * (unsigned)m);
+  const unsigned sl = e / mg;
+  const int j0 = (int)(e - sl * mg) * NC;
   const int tl = (int)(sl / (unsigned)g.Vs);
   const int ms = (int)(sl - (unsigned)tl * (unsigned)g.Vs);
-  const R alpha = (R)coef[3 * tl], beta = (R)coef[3 * tl + 1], gamma = (R)coef[3 * tl + 2];
+  const A alpha = (A)coef[3 * tl], beta = (A)coef[3 * tl + 1], gamma = (A)coef[3 * tl + 2];
   const size_t rowbase = (size_t)tl * g.Vs;
-  Cx<R> res[3];
+  Cx<A> res[3][NC];
 #pragma unroll
-  for (int a = 0; a < 3; a++) res[a] = cx<R>(0, 0);
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int c = 0; c < NC; c++) res[a][c] = cx<A>(0, 0);
   if (in) {
     const int yz = ms / g.L, x = ms - yz * g.L, z = yz / g.L, y = yz - z * g.L;
     const size_t s = (size_t)(t0 + tl) * g.Vs + ms;
-    Cx<R> own[3], acc[3];
+    Cx<A> acc[3][NC];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      own[a] = in[((rowbase + ms) * 3 + a) * m + j];
-      acc[a] = (R)6 * own[a];
+      Cx<R> v[NC];
+      ld_cols<NC>(in + ((rowbase + ms) * 3 + a) * m + j0, v);   // own term, kept for beta
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        res[a][c] = to_a<A>(v[c]);
+        acc[a][c] = (A)6 * res[a][c];
+      }
     }
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -93,38 +139,55 @@ __global__ void __launch_bounds__(256) k_lap(Geom g, int t0, int Tn, int m, cons
       else if (k == 1) { yf = y + 1 == g.L ? 0 : y + 1; yb = y == 0 ? g.L - 1 : y - 1; }
       else { zf = z + 1 == g.L ? 0 : z + 1; zb = z == 0 ? g.L - 1 : z - 1; }
       const int mf = xf + g.L * (yf + g.L * zf), mb = xb + g.L * (yb + g.L * zb);
-      Cx<R> uf[3][3], ub[3][3], vf[3], vb[3];
+      Cx<A> uf[3][3], ub[3][3];
       load_link3(U, k, s, (size_t)g.V, uf);
       load_link3(U, k, (size_t)(t0 + tl) * g.Vs + mb, (size_t)g.V, ub);
+      Cx<R> vf[3][NC], vb[3][NC];
 #pragma unroll
       for (int a = 0; a < 3; a++) {
-        vf[a] = in[((rowbase + mf) * 3 + a) * m + j];
-        vb[a] = in[((rowbase + mb) * 3 + a) * m + j];
+        ld_cols<NC>(in + ((rowbase + mf) * 3 + a) * m + j0, vf[a]);
+        ld_cols<NC>(in + ((rowbase + mb) * 3 + a) * m + j0, vb[a]);
       }
 #pragma unroll
-      for (int a = 0; a < 3; a++) {
-        Cx<R> h = cx<R>(0, 0);
+      for (int c = 0; c < NC; c++)
 #pragma unroll
-        for (int b = 0; b < 3; b++) {
-          fma_acc(h, uf[a][b], vf[b]);
-          fma_conj_acc(h, ub[b][a], vb[b]);
+        for (int a = 0; a < 3; a++) {
+          Cx<A> h = cx<A>(0, 0);
+#pragma unroll
+          for (int b = 0; b < 3; b++) {
+            fma_acc(h, uf[a][b], to_a<A>(vf[b][c]));
+            fma_conj_acc(h, ub[b][a], to_a<A>(vb[b][c]));
+          }
+          acc[a][c] = acc[a][c] - h;
         }
-        acc[a] = acc[a] - h;
-      }
     }
 #pragma unroll
-    for (int a = 0; a < 3; a++) res[a] = alpha * acc[a] + beta * own[a];
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int c = 0; c < NC; c++) res[a][c] = alpha * acc[a][c] + beta * res[a][c];
   }
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    const size_t idx = ((rowbase + ms) * 3 + a) * m + j;
-    if (prev) res[a] = res[a] + gamma * prev[idx];
-    if (rin) {
-      const R f = alpha * (R)scol[(size_t)tl * m + j];
-      const Cx<float> r = rin[idx];
-      res[a] = res[a] + f * cx<R>((R)r.re, (R)r.im);
+    const size_t idx = ((rowbase + ms) * 3 + a) * m + j0;
+    if (prev) {
+      Cx<R> pv[NC];
+      ld_cols<NC>(prev + idx, pv);
+#pragma unroll
+      for (int c = 0; c < NC; c++) res[a][c] = res[a][c] + gamma * to_a<A>(pv[c]);
     }
-    out[idx] = res[a];
+    if (rin) {
+      Cx<float> rv[NC];
+      ld_cols<NC>(rin + idx, rv);
+#pragma unroll
+      for (int c = 0; c < NC; c++) {
+        const A f = alpha * (A)scol[(size_t)tl * m + j0 + c];
+        res[a][c] = res[a][c] + f * cx<A>((A)rv[c].re, (A)rv[c].im);
+      }
+    }
+    Cx<R> o[NC];
+#pragma unroll
+    for (int c = 0; c < NC; c++) o[c] = to_s<R>(res[a][c]);
+    st_cols<NC>(out + idx, o);
   }
 }
 
@@ -132,11 +195,11 @@ __global__ void __launch_bounds__(256) k_lap(Geom g, int t0, int Tn, int m, cons
 // herm: the product is hermitian (X^dag X, or Y^dag A Y with A hermitian): only the
 // tiles on and above the diagonal are computed, k_gram_reduce mirrors the rest
 constexpr int GT = 32, GKS = 32;
-template <class R>
+template <class R, class A>
 __global__ void __launch_bounds__(256) k_gram(const Cx<R>* __restrict__ X, const Cx<R>* __restrict__ Y, int n, int m,
                                               int nsplit, int herm, double2* part) {
-  __shared__ Cx<R> xs[GKS][GT + 1];
-  __shared__ Cx<R> ys[GKS][GT + 1];
+  __shared__ Cx<A> xs[GKS][GT + 1];
+  __shared__ Cx<A> ys[GKS][GT + 1];
   const int tiles_j = (m + GT - 1) / GT;
   int ti = blockIdx.x / tiles_j, tj = blockIdx.x % tiles_j;
   if (herm) {                 // blockIdx.x enumerates the pairs ti <= tj row by row
@@ -152,11 +215,11 @@ __global__ void __launch_bounds__(256) k_gram(const Cx<R>* __restrict__ X, const
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4, tid = threadIdx.x;
   const Cx<R>* Xt = X + (size_t)t * n * m;
   const Cx<R>* Yt = Y + (size_t)t * n * m;
-  Cx<R> acc[2][2];
+  Cx<A> acc[2][2];
 #pragma unroll
   for (int a = 0; a < 2; a++)
 #pragma unroll
-    for (int b = 0; b < 2; b++) acc[a][b] = cx<R>(0, 0);
+    for (int b = 0; b < 2; b++) acc[a][b] = cx<A>(0, 0);
   for (int kb = k0; kb < k1; kb += GKS) {
 #pragma unroll
     for (int q = 0; q < (GKS * GT) / 256; q++) {
@@ -168,13 +231,13 @@ __global__ void __launch_bounds__(256) k_gram(const Cx<R>* __restrict__ X, const
         if (i0 + c < m) vx = Xt[(size_t)k * m + i0 + c];
         if (j0 + c < m) vy = Yt[(size_t)k * m + j0 + c];
       }
-      xs[r][c] = vx;
-      ys[r][c] = vy;
+      xs[r][c] = to_a<A>(vx);
+      ys[r][c] = to_a<A>(vy);
     }
     __syncthreads();
 #pragma unroll 8
     for (int r = 0; r < GKS; r++) {
-      const Cx<R> x0 = xs[r][ty], x1 = xs[r][ty + 16], y0 = ys[r][tx], y1 = ys[r][tx + 16];
+      const Cx<A> x0 = xs[r][ty], x1 = xs[r][ty + 16], y0 = ys[r][tx], y1 = ys[r][tx + 16];
       fma_conj_acc(acc[0][0], x0, y0);
       fma_conj_acc(acc[0][1], x0, y1);
       fma_conj_acc(acc[1][0], x1, y0);
@@ -212,36 +275,36 @@ __global__ void k_gram_reduce(const double2* part, int nsplit, int m, int Tn, in
 
 // rotation Z_t = X_t C_t (X_t n x m row-major, C_t m x m row-major FP64); 64 x 64 output tiles
 constexpr int RT = 64, RL = 16;
-template <class R>
+template <class R, class A>
 __global__ void __launch_bounds__(256) k_rotate(const Cx<R>* __restrict__ X, const double2* __restrict__ Cm, int n,
                                                 int m, Cx<R>* __restrict__ Z) {
-  __shared__ Cx<R> xs[RT][RL + 1];
-  __shared__ Cx<R> cs[RL][RT + 1];
+  __shared__ Cx<A> xs[RT][RL + 1];
+  __shared__ Cx<A> cs[RL][RT + 1];
   const int t = blockIdx.z, k0 = blockIdx.x * RT, j0 = blockIdx.y * RT;
   const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
   const Cx<R>* Xt = X + (size_t)t * n * m;
   const double2* C = Cm + (size_t)t * m * m;
-  Cx<R> acc[4][4];
+  Cx<A> acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; a++)
 #pragma unroll
-    for (int b = 0; b < 4; b++) acc[a][b] = cx<R>(0, 0);
+    for (int b = 0; b < 4; b++) acc[a][b] = cx<A>(0, 0);
   for (int l0 = 0; l0 < m; l0 += RL) {
 #pragma unroll
     for (int q = 0; q < (RT * RL) / 256; q++) {
       const int e = tid + 256 * q;
       const int r = e / RL, c = e % RL;
       const int k = k0 + r, l = l0 + c;
-      xs[r][c] = (k < n && l < m) ? Xt[(size_t)k * m + l] : cx<R>(0, 0);
+      xs[r][c] = (k < n && l < m) ? to_a<A>(Xt[(size_t)k * m + l]) : cx<A>(0, 0);
       const int r2 = e / RT, c2 = e % RT;
       const int l2 = l0 + r2, j2 = j0 + c2;
       double2 cv = (l2 < m && j2 < m) ? C[(size_t)l2 * m + j2] : make_double2(0, 0);
-      cs[r2][c2] = cx<R>((R)cv.x, (R)cv.y);
+      cs[r2][c2] = cx<A>((A)cv.x, (A)cv.y);
     }
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < RL; l++) {
-      Cx<R> xv[4], cv[4];
+      Cx<A> xv[4], cv[4];
 #pragma unroll
       for (int a = 0; a < 4; a++) xv[a] = xs[tr + 16 * a][l];
 #pragma unroll
@@ -259,7 +322,7 @@ __global__ void __launch_bounds__(256) k_rotate(const Cx<R>* __restrict__ X, con
 #pragma unroll
     for (int b = 0; b < 4; b++) {
       const int k = k0 + tr + 16 * a, j = j0 + tc + 16 * b;
-      if (k < n && j < m) Zt[(size_t)k * m + j] = acc[a][b];
+      if (k < n && j < m) Zt[(size_t)k * m + j] = to_s<R>(acc[a][b]);
     }
 }
 
@@ -398,6 +461,7 @@ __global__ void k_lap_canonical(Geom g, const double2* __restrict__ U3, const do
 struct Eig {
   dlma_ctx* ctx;
   int t0, Tn, N, m, n, nsplit, degree;
+  int df = 0;   // phase B: Gram matrices and rotations in double-float (tol >= 1e-11)
   size_t blk;                    // m * Tn * n complex entries per block
   Cx<float> *F0, *F1, *F2, *F3;  // FP32 blocks
   Cx<double> *D0, *D1, *D2;      // FP64 blocks
@@ -430,8 +494,15 @@ static dlma_status lap(Eig& E, const Cx<R>* in, const Cx<R>* prev, const Cx<floa
   const size_t total = (size_t)E.Tn * ctx->g.Vs * E.m;
   if (total >= (1ull << 31)) return set_err(ctx, DLMA_ERR_INVALID_ARG, "eigensolver block above 2^31 entries");
   phase(E, kPhMatvec);
-  k_lap<R><<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(ctx->g, E.t0, E.Tn, E.m, links<R>(ctx), in, prev,
-                                                                     rin, scol, out, coef);
+  // m is even; FP32: two columns per thread (one 128-bit access per pair, links
+  // rebuilt once per pair); FP64 is bound by its arithmetic and keeps one
+  if constexpr (sizeof(R) == 4) {
+    k_lap<R, R, 2><<<(unsigned)((total / 2 + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->g, E.t0, E.Tn, E.m, links<R>(ctx), in, prev, rin, scol, out, coef);
+  } else {
+    k_lap<R, R, 1><<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(ctx->g, E.t0, E.Tn, E.m, links<R>(ctx), in,
+                                                                             prev, rin, scol, out, coef);
+  }
   CHECK_LAUNCH();
   return DLMA_OK;
 }
@@ -442,7 +513,13 @@ template <class R> static dlma_status gram(Eig& E, const Cx<R>* X, const Cx<R>* 
   const int tj = (E.m + GT - 1) / GT;
   const int tiles = herm ? tj * (tj + 1) / 2 : tj * tj;
   phase(E, kPhOrtho);
-  k_gram<R><<<dim3(tiles, E.nsplit, E.Tn), 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, herm, E.part);
+  const dim3 grid(tiles, E.nsplit, E.Tn);
+  if constexpr (sizeof(R) == 8) {
+    if (E.df) k_gram<R, df><<<grid, 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, herm, E.part);
+    else k_gram<R, R><<<grid, 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, herm, E.part);
+  } else {
+    k_gram<R, R><<<grid, 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, herm, E.part);
+  }
   CHECK_LAUNCH();
   const size_t tot = (size_t)E.m * E.m * E.Tn;
   k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(E.part, E.nsplit, E.m, E.Tn, herm, out);
@@ -453,14 +530,21 @@ template <class R> static dlma_status gram(Eig& E, const Cx<R>* X, const Cx<R>* 
 template <class R> static dlma_status rotate(Eig& E, const Cx<R>* X, Cx<R>* Z) {
   dlma_ctx* ctx = E.ctx;
   phase(E, kPhOrtho);
-  k_rotate<R><<<dim3((E.n + RT - 1) / RT, (E.m + RT - 1) / RT, E.Tn), 256, 0, ctx->stream>>>(X, E.C, E.n, E.m, Z);
+  const dim3 grid((E.n + RT - 1) / RT, (E.m + RT - 1) / RT, E.Tn);
+  if constexpr (sizeof(R) == 8) {
+    if (E.df) k_rotate<R, df><<<grid, 256, 0, ctx->stream>>>(X, E.C, E.n, E.m, Z);
+    else k_rotate<R, R><<<grid, 256, 0, ctx->stream>>>(X, E.C, E.n, E.m, Z);
+  } else {
+    k_rotate<R, R><<<grid, 256, 0, ctx->stream>>>(X, E.C, E.n, E.m, Z);
+  }
   CHECK_LAUNCH();
   return DLMA_OK;
 }
 
-// small Rayleigh-Ritz problems in precision T (float in phase A, double in phase B,
-// where the column-scaled block has a well-conditioned Gram matrix and the
-// orthonormalisation takes the Cholesky route)
+// small Rayleigh-Ritz problems in precision T (float in phase A, double in phase B).
+// The orthonormalisation tries the Cholesky route first in both phases; a pivot
+// below the precision's floor (an ill-conditioned Gram matrix, as the unscaled
+// phase-A block can have) falls back to the Jacobi route inside the kernel.
 template <class T> static dlma_status small_rr(Eig& E) {
   dlma_ctx* ctx = E.ctx;
   const size_t sm = (size_t)3 * E.m * (E.m + 1) * sizeof(Cx<T>);   // three m x (m + 1) work matrices
@@ -469,7 +553,7 @@ template <class T> static dlma_status small_rr(Eig& E) {
   phase(E, kPhOrtho);
   if (use_smem) CU(cudaFuncSetAttribute(k_small_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   CU(cudaMemsetAsync(E.dropped, 0, sizeof(int), ctx->stream));
-  const int chol = sizeof(T) == 8 ? 1 : 0;
+  const int chol = 1;
   k_small_rr<T><<<E.Tn, 256, use_smem ? sm : 0, ctx->stream>>>(E.G, E.H, E.m, E.C, E.theta, (Cx<T>*)E.gwork,
                                                                use_smem, E.dropped, E.drop_rel, chol);
   CHECK_LAUNCH();
@@ -694,6 +778,9 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   }
   Cx<float>* X = p3[0];
   // ---- phase B: FP64 Ritz vectors, FP32 residual-driven filter ----
+  // The FP64 blocks' Gram matrices and rotations run in double-float on the FP32
+  // units when the tolerance leaves room for its ~2^-46 rounding.
+  E.df = ctx->df_eigs && tol >= 1e-11;
   Cx<double> *X64 = E.D0, *W64 = E.D1, *Y64 = E.D2;
   // phase A's last Ritz pairs were not fetched, or hold refilled (random) columns
   const bool rr_first = E.refilled || it >= maxA;

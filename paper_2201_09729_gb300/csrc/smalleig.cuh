@@ -9,7 +9,8 @@
 // G = R^dag R, S = R^-1 (about 2 m^3 / 3 operations against three times that per
 // Jacobi sweep): for a well-conditioned G, as the FP64 phase of the eigensolver
 // produces, it replaces the first Jacobi solve; a pivot at or below the rounding
-// level of the largest diagonal falls back to the Jacobi route.
+// level of the largest diagonal falls back to the Jacobi route (the FP32 phase
+// tries it too and falls back whenever its block is ill-conditioned).
 //
 // The eigendecompositions use the parallel cyclic Jacobi method (round-robin
 // pairing, m/2 disjoint complex rotations per round).  T = float serves the

@@ -935,6 +935,28 @@ static dlma_status solve_finish(dlma_ctx* ctx, SolveBufs& B, double* x_dev, int 
 // The host launches the graph once and waits by polling with a wall-clock
 // limit; at the limit it raises a stop flag in pinned memory that k_loop reads,
 // so the graph ends after the pass in flight and no wait is unbounded.
+// With ctx->solve_graph == 0 (DLMA_SOLVE_GRAPH=0 at context creation) the same
+// passes are launched from the host one by one, each followed by a count of the
+// iterating rhs: the same kernels and arithmetic, visible one by one to kernel
+// profilers that do not look inside conditional graphs.
+template <class Body, class Update>
+static dlma_status iterate_host(dlma_ctx* ctx, SolveBufs& B, int nrhs, int max_inner, int chunk, Body body,
+                                Update update) {
+  int* hcount = (int*)ctx->pinned;
+  const int max_chunks = std::max(1, max_inner / chunk);
+  for (int pass = 0; pass < max_chunks; pass++) {
+    for (int k = 0; k < chunk; k++) TRY(body());
+    TRY(update(false));
+    k_count<<<1, 256, 0, ctx->stream>>>(B.sc.active, B.sc.ru, nrhs, B.sc.count);
+    CHECK_LAUNCH();
+    CU(cudaMemcpyAsync(hcount, B.sc.count, 8 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (hcount[1]) return set_err(ctx, DLMA_ERR_NONFINITE, "non-finite value in the solve");
+    if (hcount[0] == 0 && hcount[2] == 0) return DLMA_OK;
+  }
+  return set_err(ctx, DLMA_ERR_NOT_CONVERGED, "iteration cap %d reached", max_inner);
+}
+
 template <class Body, class Update>
 static dlma_status iterate(dlma_ctx* ctx, SolveBufs& B, int nrhs, int max_inner, Body body, Update update) {
   volatile int* hpin = (volatile int*)ctx->pinned;   // [0..7] counts (copied back), [16] stop flag
@@ -943,6 +965,7 @@ static dlma_status iterate(dlma_ctx* ctx, SolveBufs& B, int nrhs, int max_inner,
   const double wall_limit_s = 600.0;
   TRY(update(true));
   CU(cudaMemsetAsync(B.sc.count, 0, 8 * sizeof(int), ctx->stream));
+  if (!ctx->solve_graph) return iterate_host(ctx, B, nrhs, max_inner, chunk, body, update);
   hpin[16] = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
