@@ -97,6 +97,7 @@ struct dlma_ctx {
   // stencil block shape (sites x right-hand sides) per precision, chosen by autotune_hop
   int hop_sx[3] = {64, 64, 64}, hop_sy[3] = {4, 4, 4}, hop_tuned[3] = {0, 0, 0};
   int hop_l18[3] = {0, 0, 0};   // FP32: read 18-real links instead of rebuilding row 2
+  int hop_chunk[3] = {64, 64, 64};   // right-hand sides per chunk of the stencil's block order
   int hop_nr[3] = {1, 1, 1};    // FP32: right-hand sides per thread (1 or 2)
   // the Laplacian eigensolver's FP64 phase computes its Gram matrices and rotations
   // in double-float (dfloat.cuh) for tol >= 1e-11; DLMA_DF_EIGS=0 at context

@@ -402,49 +402,75 @@ __global__ void __launch_bounds__(128) k_noise_parts_dil(const double2* __restri
   }
 }
 
+// The spin matrices A = g5 G and B = G g5 of the four channels are permutations
+// with phases (one nonzero per row and column): for channel ch, row a of A has its
+// entry in column bOf[ch][a], and column beta of B its entry in row bpOf[ch][beta].
+struct SrcPerm {
+  int bOf[4][4], bpOf[4][4];
+  double2 av[4][4], bv[4][4];
+};
+static bool src_perm(const SpinMats& S, SrcPerm* P) {
+  for (int ch = 0; ch < 4; ch++)
+    for (int i = 0; i < 4; i++) {
+      int na = 0, nb = 0;
+      for (int j = 0; j < 4; j++) {
+        if (S.re[ch][i][j] != 0.0 || S.im[ch][i][j] != 0.0) {
+          P->bOf[ch][i] = j;
+          P->av[ch][i] = make_double2(S.re[ch][i][j], S.im[ch][i][j]);
+          na++;
+        }
+        if (S.re[4 + ch][j][i] != 0.0 || S.im[4 + ch][j][i] != 0.0) {
+          P->bpOf[ch][i] = j;
+          P->bv[ch][i] = make_double2(S.re[4 + ch][j][i], S.im[4 + ch][j][i]);
+          nb++;
+        }
+      }
+      if (na != 1 || nb != 1) return false;
+    }
+  return true;
+}
+
 // Per mode k and timeslice t: sum_{beta,beta'} B[beta'][beta] sum_{x in t} sum_{a,b}
-// A[a][b] conj(phi^{(k,beta)}(x,a,.)) . phi^{(k,beta')}(x,b,.) for the four channels
-// (A = g5 G, B = G g5).  The four solutions of mode k are rows 4 k .. 4 k + 3 of
-// psi (batch-relative).  Zero entries of A and B are skipped by uniform branches.
+// A[a][b] conj(phi^{(k,beta)}(x,a,.)) . phi^{(k,beta')}(x,b,.) for the four channels.
+// The four solutions of mode k are rows 4 k .. 4 k + 3 of psi (batch-relative).  One
+// thread per (site, beta): it holds phi^{(k,beta)} and reads, per channel, the one
+// phi^{(k,beta')} that B pairs with it (no branches on the spin structure).
 __global__ void __launch_bounds__(128) k_src_box(const double2* __restrict__ psi, size_t stride_sites, int Vs,
-                                                 SpinMats S, int k0, double2* part, int T) {
+                                                 SrcPerm P, int k0, double2* part, int T) {
   const int t = blockIdx.x, kl = blockIdx.y;
+  const int bt = threadIdx.x & 3;
   Cx<double> acc[4];
 #pragma unroll
   for (int ch = 0; ch < 4; ch++) acc[ch] = cx<double>(0, 0);
-  for (int m = threadIdx.x; m < Vs; m += blockDim.x) {
-    Cx<double> f[4][12];
-#pragma unroll
-    for (int b = 0; b < 4; b++) {
-      const double2* p = psi + ((size_t)(4 * kl + b) * stride_sites + (size_t)t * Vs + m) * 12;
+  for (int m = threadIdx.x >> 2; m < Vs; m += blockDim.x >> 2) {
+    const size_t site = (size_t)t * Vs + m;
+    Cx<double> ft[12];
+    {
+      const double2* p = psi + ((size_t)(4 * kl + bt) * stride_sites + site) * 12;
 #pragma unroll
       for (int q = 0; q < 12; q++) {
         const double2 e = __ldg(p + q);
-        f[b][q] = cx<double>(e.x, e.y);
+        ft[q] = cx<double>(e.x, e.y);
       }
     }
 #pragma unroll
-    for (int ch = 0; ch < 4; ch++)
+    for (int ch = 0; ch < 4; ch++) {
+      const int bp = P.bpOf[ch][bt];
+      const double2* pp = psi + ((size_t)(4 * kl + bp) * stride_sites + site) * 12;
+      Cx<double> inner = cx<double>(0, 0);
 #pragma unroll
-      for (int bp = 0; bp < 4; bp++)
+      for (int a = 0; a < 4; a++) {
+        const int b = P.bOf[ch][a];
+        Cx<double> d = cx<double>(0, 0);
 #pragma unroll
-        for (int bt = 0; bt < 4; bt++) {
-          const Cx<double> Bv = cx<double>(S.re[4 + ch][bp][bt], S.im[4 + ch][bp][bt]);
-          if (Bv.re == 0.0 && Bv.im == 0.0) continue;
-          Cx<double> inner = cx<double>(0, 0);
-#pragma unroll
-          for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int b = 0; b < 4; b++) {
-              const Cx<double> Av = cx<double>(S.re[ch][a][b], S.im[ch][a][b]);
-              if (Av.re == 0.0 && Av.im == 0.0) continue;
-              Cx<double> d = cx<double>(0, 0);
-#pragma unroll
-              for (int c = 0; c < 3; c++) fma_conj_acc(d, f[bt][a * 3 + c], f[bp][b * 3 + c]);
-              fma_acc(inner, Av, d);
-            }
-          fma_acc(acc[ch], Bv, inner);
+        for (int c = 0; c < 3; c++) {
+          const double2 e = __ldg(pp + b * 3 + c);
+          fma_conj_acc(d, ft[a * 3 + c], cx<double>(e.x, e.y));
         }
+        fma_acc(inner, cx<double>(P.av[ch][a].x, P.av[ch][a].y), d);
+      }
+      fma_acc(acc[ch], cx<double>(P.bv[ch][bt].x, P.bv[ch][bt].y), inner);
+    }
   }
   __shared__ double red[8][128];
 #pragma unroll
@@ -658,8 +684,10 @@ static dlma_status fetch_parts(dlma_ctx* ctx, const double2* out, double* C_dist
 // are rows 0 .. 4 nk - 1 of psi: part[k][ch][t]
 static dlma_status src_box(dlma_ctx* ctx, const double* psi, int k0, int nk, double2* part) {
   if (nk < 1) return DLMA_OK;
-  k_src_box<<<dim3(ctx->g.T, nk), 128, 0, ctx->stream>>>((const double2*)psi, (size_t)ctx->g.V, ctx->g.Vs,
-                                                         spin_mats(), k0, part, ctx->g.T);
+  SrcPerm P;
+  if (!src_perm(spin_mats(), &P)) return set_err(ctx, DLMA_ERR_CUDA, "spin matrices are not permutations");
+  k_src_box<<<dim3(ctx->g.T, nk), 128, 0, ctx->stream>>>((const double2*)psi, (size_t)ctx->g.V, ctx->g.Vs, P, k0,
+                                                         part, ctx->g.T);
   CHECK_LAUNCH();
   return DLMA_OK;
 }

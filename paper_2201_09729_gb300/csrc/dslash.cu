@@ -110,12 +110,8 @@ __device__ __forceinline__ void load_clover_block(const void* __restrict__ C, in
 // arithmetic-bound and the FP16 one register-bound: both keep NR = 1.
 // hop_minb: resident blocks of 256 threads per SM the kernels are compiled for
 // (their register cap: 85 registers at 3, 128 at 2).
-// right-hand sides per chunk of the block order (see k_hop); on the 16^3 x 32 solve
-// 64 measured best of {16, 32, 64, unchunked}
-#ifndef DLMA_HOP_CHUNK
-#define DLMA_HOP_CHUNK 64
-#endif
-constexpr int kHopChunkRhs = DLMA_HOP_CHUNK;
+// Right-hand sides per chunk of the block order (see k_hop): chosen per precision
+// by the autotuner among {16, 32, 64, 128} (ctx->hop_chunk).
 constexpr int hop_minb(int P, int NR) { return P == DLMA_FP64 ? 2 : (NR > 1 ? 2 : 3); }
 
 // ---------------------------------------------------------------------------
@@ -582,7 +578,7 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   const int nr = (P == DLMA_FP32 && !cgu) ? ctx->hop_nr[P] : 1;
   a.ntiles = (ctx->g.Vh + sx - 1) / sx;
   a.ngroups = (out.nrhs + sy * nr - 1) / (sy * nr);
-  a.gpc = std::max(1, std::min(a.ngroups, kHopChunkRhs / (sy * nr)));
+  a.gpc = std::max(1, std::min(a.ngroups, ctx->hop_chunk[P] / (sy * nr)));
   const int nchunks = (a.ngroups + a.gpc - 1) / a.gpc;
   dim3 grid((unsigned)((size_t)nchunks * a.ntiles * a.gpc));
   if (nblocks_out) *nblocks_out = a.ntiles;
@@ -621,7 +617,9 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
 }
 
 // Autotuner: time the Schur operator (both hop launches) on the caller's own
-// fields for each candidate block shape and keep the fastest for this precision.
+// fields for each candidate block shape (and, in FP32, link format and right-hand
+// sides per thread), then for each chunk size of the block order, and keep the
+// fastest for this precision.
 dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, Field& out) {
   if (ctx->hop_tuned[prec]) return DLMA_OK;
   static const int cand[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}, {32, 2}};
@@ -665,6 +663,33 @@ dlma_status autotune_hop(dlma_ctx* ctx, int prec, const Field& in, Field& tmp, F
   ctx->hop_sy[prec] = by;
   ctx->hop_l18[prec] = bl;
   ctx->hop_nr[prec] = bn;
+  // then the chunk of the block order: how many right-hand sides sweep the lattice
+  // together (their neighbour spinors must stay in L2 between uses);
+  // DLMA_FORCE_CHUNK pins it (profiling)
+  int bc = ctx->hop_chunk[prec];
+  best = 1e30f;
+  int chunks[4] = {16, 32, 64, 128}, nch = 4;
+  if (const char* f = getenv("DLMA_FORCE_CHUNK")) {
+    chunks[0] = std::max(1, atoi(f));
+    nch = 1;
+  }
+  for (int q = 0; q < nch; q++) {
+    const int ch = chunks[q];
+    if (nch == 1) { bc = ch; break; }
+    ctx->hop_chunk[prec] = ch;
+    float tot = 0;
+    for (int r = 0; r < 3; r++) {
+      CU(cudaEventRecord(e0, ctx->stream));
+      TRY(schur_apply(ctx, in, tmp, out, 0, nullptr, nullptr));
+      CU(cudaEventRecord(e1, ctx->stream));
+      CU(cudaEventSynchronize(e1));
+      float ms = 0;
+      CU(cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0) tot += ms;
+    }
+    if (tot < best) { best = tot; bc = ch; }
+  }
+  ctx->hop_chunk[prec] = bc;
   ctx->hop_tuned[prec] = 1;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -41,6 +41,12 @@ template <class T>
 __device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, int ld, T* rc, T* rs, Cx<T>* re, double* red) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int np = m / 2;
+  // thread layout of the row / column updates: rows i0 + l ni, pairs k0 + l nk (no
+  // integer division per element)
+  const int ni = m <= nt ? m : nt, nk = m <= nt ? nt / m : 1;
+  const int i0 = tid % ni, k0 = tid / ni;
+  const bool upd = k0 < nk;
+  __shared__ int pq[2][kSmallMaxM / 2];
   __shared__ int rotated;
   __shared__ double dmax;
   if (tid == 0) {
@@ -58,6 +64,8 @@ __device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, int ld, T* rc, T* rs, Cx<T>* re
     for (int r = 0; r < m - 1; r++) {
       for (int k = tid; k < np; k += nt) {
         const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
+        pq[0][k] = p;
+        pq[1][k] = q;
         const T a = A[p * ld + p].re, d = A[q * ld + q].re;
         const Cx<T> b = A[p * ld + q];
         const T ab = sqrt(b.re * b.re + b.im * b.im);
@@ -74,30 +82,36 @@ __device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, int ld, T* rc, T* rs, Cx<T>* re
         re[k] = cx<T>(b.re / ab, -b.im / ab);   // e^{-i phi}
       }
       __syncthreads();
-      for (int e = tid; e < np * m; e += nt) {        // A <- A J, V <- V J (columns p, q)
-        const int k = e / m, i = e % m;
-        if (rs[k] == (T)0) continue;                  // pair not rotated this round
-        const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
-        const T c = rc[k], s = rs[k];
-        const Cx<T> ph = re[k];
-        const Cx<T> ap = A[i * ld + p], aq = ph * A[i * ld + q];
-        A[i * ld + p] = c * ap - s * aq;
-        A[i * ld + q] = s * ap + c * aq;
-        const Cx<T> vp = V[i * ld + p], vq = ph * V[i * ld + q];
-        V[i * ld + p] = c * vp - s * vq;
-        V[i * ld + q] = s * vp + c * vq;
-      }
+      if (upd)
+        for (int k = k0; k < np; k += nk) {          // A <- A J, V <- V J (columns p, q)
+          const T s = rs[k];
+          if (s == (T)0) continue;                     // pair not rotated this round
+          const int p = pq[0][k], q = pq[1][k];
+          const T c = rc[k];
+          const Cx<T> ph = re[k];
+          for (int i = i0; i < m; i += ni) {
+            const Cx<T> ap = A[i * ld + p], aq = ph * A[i * ld + q];
+            A[i * ld + p] = c * ap - s * aq;
+            A[i * ld + q] = s * ap + c * aq;
+            const Cx<T> vp = V[i * ld + p], vq = ph * V[i * ld + q];
+            V[i * ld + p] = c * vp - s * vq;
+            V[i * ld + q] = s * vp + c * vq;
+          }
+        }
       __syncthreads();
-      for (int e = tid; e < np * m; e += nt) {        // A <- J^dag A (rows p, q)
-        const int k = e / m, j = e % m;
-        if (rs[k] == (T)0) continue;
-        const int p = rr_pos(k, r, m), q = rr_pos(m - 1 - k, r, m);
-        const T c = rc[k], s = rs[k];
-        const Cx<T> ph = conj(re[k]);
-        const Cx<T> ap = A[p * ld + j], aq = ph * A[q * ld + j];
-        A[p * ld + j] = c * ap - s * aq;
-        A[q * ld + j] = s * ap + c * aq;
-      }
+      if (upd)
+        for (int k = k0; k < np; k += nk) {          // A <- J^dag A (rows p, q)
+          const T s = rs[k];
+          if (s == (T)0) continue;
+          const int p = pq[0][k], q = pq[1][k];
+          const T c = rc[k];
+          const Cx<T> ph = conj(re[k]);
+          for (int j = i0; j < m; j += ni) {
+            const Cx<T> ap = A[p * ld + j], aq = ph * A[q * ld + j];
+            A[p * ld + j] = c * ap - s * aq;
+            A[q * ld + j] = s * ap + c * aq;
+          }
+        }
       __syncthreads();
     }
     if (!rotated) break;      // every pair below the threshold: converged

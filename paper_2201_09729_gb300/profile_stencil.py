@@ -7,7 +7,8 @@ synthetic gauge field for profiling, e.g.
 Prints the CUDA-event time of each application and the algorithmic bytes.
 With --sweep, every FP32 variant the autotuner chooses from (one or two
 right-hand sides per thread, 12- or 18-real links; each with its best block
-shape) is timed in a fresh context and reported.
+shape) is timed in a fresh context and reported; with --chunks, every chunk
+size of the block order (DLMA_FORCE_CHUNK).
 """
 import argparse
 import os
@@ -25,6 +26,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp16s"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--chunks", action="store_true", help="time each chunk size of the block order")
     a = ap.parse_args()
     import torch
 
@@ -42,6 +44,21 @@ def main():
     g = torch.Generator(device="cuda").manual_seed(1)
     v = torch.randn((a.nrhs, Vh, 4, 3), dtype=torch.complex128, device="cuda", generator=g)
     by = schur_bytes(Vh, a.nrhs, a.prec)
+    if a.chunks:
+        ctx.close()
+        for ch in (16, 32, 64, 128):
+            os.environ["DLMA_FORCE_CHUNK"] = str(ch)
+            c = Context(a.L, a.T, 0, 0)
+            c.dlma_set_gauge(U)
+            c.dlma_set_params(1 / (2 * 0.1225) - 4, 1.0)
+            ms = []
+            for r in range(a.reps + 1):
+                c.dlma_apply_schur(v, 0, prec)
+                ms.append(c.dlma_last_timing()[0])
+            best = min(ms[1:])
+            print(f"chunk {ch}: best {best:.3f} ms  {by / best / 1e6:.1f} GB/s algorithmic")
+            c.close()
+        return
     if a.sweep:
         ctx.close()
         for nr, links in ((1, 12), (1, 18), (2, 12), (2, 18)):

@@ -78,6 +78,28 @@ def test_schur_fp32_link_formats(dl, links, monkeypatch):
             assert _rel(got[j], want[j]) < 1e-6
 
 
+def test_schur_block_order_chunks_bit_identical(dl, monkeypatch):
+    # the chunk size of the stencil's block order only reorders the blocks: every
+    # output element is computed by one thread with the same operations, so 16 and
+    # 128 right-hand sides per chunk (ragged against 37 right-hand sides, two per
+    # thread) give identical bits, FP32 and FP64, and match the oracle
+    L, T = 6, 4
+    ve = synth.gaussian_spinors(37, L ** 3 * T // 2, 113)
+    out = {}
+    for ch in ("16", "128"):
+        monkeypatch.setenv("DLMA_FORCE_CHUNK", ch)
+        monkeypatch.setenv("DLMA_FORCE_NR", "2")
+        ctx, eo = _ctx(dl, L, T, 0.25, 0.1, 1.2, 111)
+        out[ch] = (ctx.dlma_apply_schur(ve, 0, dl.FP32), ctx.dlma_apply_schur(ve, 0, dl.FP64))
+        ctx.close()
+    want = eo.schur(ve)
+    for k in (0, 1):
+        assert np.array_equal(out["16"][k], out["128"][k])
+    for j in range(37):
+        assert _rel(out["16"][0][j], want[j]) < 1e-6
+        assert _rel(out["16"][1][j], want[j]) < 1e-13
+
+
 @pytest.mark.parametrize("dagger", [0, 1])
 def test_schur_fp64(dl, dagger):
     L, T = 6, 4
