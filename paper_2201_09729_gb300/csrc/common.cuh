@@ -172,7 +172,7 @@ enum WorkSlot {
   WS_EIG_X, WS_EIG_Y, WS_EIG_Y2, WS_EIG_W, WS_EIG_G, WS_EIG_PART, WS_EIG_S, WS_EIG_AUX,
   WS_PROJ_V, WS_PROJ_PART, WS_PROJ_C, WS_CON, WS_CON2, WS_SRC, WS_SOL, WS_ETA,
   WS_BI_S, WS_BI_R0, WS_BI_PART, WS_BI_SCAL, WS_RETRY_B, WS_RETRY_X,
-  WS_TC_A, WS_TC_B, WS_TC_E,
+  WS_TC_A, WS_TC_B, WS_TC_E, WS_SUPPORT,
   WS_COUNT
 };
 
@@ -266,6 +266,10 @@ struct HopOp {
   // partial of sum conj(w) out into dot_part; w is a field in the output precision
   const struct Field* dot_w = nullptr;
   double2* dot_part = nullptr;
+  // output sites: the compressed indices site0 .. site0 + nsites - 1 (cyclic modulo
+  // V/2; nsites < 0: all).  Whole timeslices are contiguous ranges, so a source
+  // supported on few timeslices needs few sites; no partial sums with a range.
+  int site0 = 0, nsites = -1;
 };
 dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Field* own, Field& out,
                        int* nblocks_out = nullptr);

@@ -128,6 +128,7 @@ struct HopArgs {
   const int* active;
   const int4* nbr;    // neighbour table (dlma_ctx::nbr_tab)
   int l18;            // FP32: Ua holds 18-real links
+  int site0, nsites;   // output sites site0 .. site0 + nsites - 1 (cyclic modulo Vh)
   // CG epilogue (CGU): with z the result at this site, x += alpha p, r -= alpha z
   // (vector precision PB = FP64 for an FP64 stencil, FP32 otherwise), partial |r|^2
   void* cg_x; void* cg_r; const void* cg_p; const double* cg_alpha; size_t cg_stride;
@@ -260,7 +261,9 @@ __global__ void __launch_bounds__(256, hop_minb(P, NR)) k_hop(HopArgs a) {
   const int per_chunk = a.ntiles * a.gpc;
   const int chunk = blockIdx.x / per_chunk, rem = blockIdx.x - chunk * per_chunk;
   const int tile = rem / a.gpc, grp = chunk * a.gpc + (rem - (rem / a.gpc) * a.gpc);
-  const int i = tile * blockDim.x + threadIdx.x;
+  const int il = tile * blockDim.x + threadIdx.x;       // index within the site range
+  int i = a.site0 + il;
+  if (i >= a.g.Vh) i -= a.g.Vh;
   const int j0 = (grp * blockDim.y + threadIdx.y) * NR;
   const Geom g = a.g;
   int jq[NR];
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(256, hop_minb(P, NR)) k_hop(HopArgs a) {
 #pragma unroll
   for (int q = NR - 1; q >= 0; q--) {
     jq[q] = j0 + q;
-    vq[q] = i < g.Vh && jq[q] < a.nrhs && (!a.active || a.active[jq[q]] != 0);
+    vq[q] = il < a.nsites && jq[q] < a.nrhs && (!a.active || a.active[jq[q]] != 0);
     if (vq[q]) { valid = true; jany = jq[q]; }
   }
   // loads of an idle slot read a live right-hand side of this thread (always in bounds)
@@ -576,7 +579,13 @@ dlma_status launch_hop(dlma_ctx* ctx, const HopOp& op, const Field& in, const Fi
   const bool cgu = op.cg_x != nullptr && op.hop;
   const bool dot = op.dot_part != nullptr && op.hop && op.own == 2 && !op.kout && !op.g5_hop;
   const int nr = (P == DLMA_FP32 && !cgu) ? ctx->hop_nr[P] : 1;
-  a.ntiles = (ctx->g.Vh + sx - 1) / sx;
+  if (op.nsites >= 0 && (op.norm_part || op.dot_part || op.cg_x || op.nsites > ctx->g.Vh || op.site0 < 0 ||
+                         op.site0 >= ctx->g.Vh))
+    return set_err(ctx, DLMA_ERR_INVALID_ARG, "stencil site range");
+  a.site0 = op.nsites >= 0 ? op.site0 : 0;
+  a.nsites = op.nsites >= 0 ? op.nsites : ctx->g.Vh;
+  if (a.nsites == 0) return DLMA_OK;
+  a.ntiles = (a.nsites + sx - 1) / sx;
   a.ngroups = (out.nrhs + sy * nr - 1) / (sy * nr);
   a.gpc = std::max(1, std::min(a.ngroups, ctx->hop_chunk[P] / (sy * nr)));
   const int nchunks = (a.ngroups + a.gpc - 1) / a.gpc;

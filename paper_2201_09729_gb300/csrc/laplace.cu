@@ -496,6 +496,9 @@ static dlma_status lap(Eig& E, const Cx<R>* in, const Cx<R>* prev, const Cx<floa
   phase(E, kPhMatvec);
   // m is even; FP32: two columns per thread (one 128-bit access per pair, links
   // rebuilt once per pair); FP64 is bound by its arithmetic and keeps one
+  // (measured alternatives: four FP32 columns per thread, 145 registers, and a
+  // double-float FP64 matvec, 170 registers and a split of every loaded value,
+  // were both slower)
   if constexpr (sizeof(R) == 4) {
     k_lap<R, R, 2><<<(unsigned)((total / 2 + 255) / 256), 256, 0, ctx->stream>>>(
         ctx->g, E.t0, E.Tn, E.m, links<R>(ctx), in, prev, rin, scol, out, coef);

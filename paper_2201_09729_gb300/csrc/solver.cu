@@ -280,6 +280,19 @@ __global__ void k_rowsum(const double* part, int nb, int nrhs, double* out, int 
 }
 
 // the paused rhs get their residual from an FP64 evaluation at this update
+// flag[t] = 1 if any right-hand side has a nonzero block partial of |.|^2 on
+// timeslice t (bpt blocks of BX sites per timeslice)
+__global__ void k_ts_support(const double* part, int nb, int nrhs, int bpt, int* flag) {
+  const int t = blockIdx.x;
+  int any = 0;
+  for (int e = threadIdx.x; e < nrhs * bpt; e += blockDim.x) {
+    const int j = e / bpt, b = t * bpt + e % bpt;
+    any |= part[(size_t)j * nb + b] != 0.0;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) flag[t] = any;
+}
+
 __global__ void k_mark_exact(int nrhs, CgScal sc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < nrhs && sc.ru[j]) sc.exact[j] = 1;
@@ -814,15 +827,67 @@ static dlma_status solve_setup(dlma_ctx* ctx, SolveBufs& B, const double* b_dev,
   k_convert<DLMA_FP64, DLMA_FP64><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.b_o.data, nullptr, B.t64o.data, nullptr,
                                                               nullptr, 0, nullptr, B.part);
   CHECK_LAUNCH();
+  // the timeslices on which b_o is nonzero (for whole-timeslice blocks)
+  const int T = ctx->g.T, hsl = ctx->g.Vs / 2;
+  const bool ts_blocks = hsl % BX == 0 && T >= 6;
+  int* dflag = nullptr;
+  std::vector<int> tsf(T, 1);
+  if (ts_blocks) {
+    TRY(workT(ctx, WS_SUPPORT, (size_t)T, &dflag));
+    k_ts_support<<<T, 256, 0, ctx->stream>>>(B.part, gv.x, nrhs, hsl / BX, dflag);
+    CHECK_LAUNCH();
+    CU(cudaMemcpyAsync(tsf.data(), dflag, sizeof(int) * T, cudaMemcpyDeviceToHost, ctx->stream));
+  }
   TRY(rowsum(ctx, B.part, gv.x, nrhs, B.tmpd + nrhs, 0, nullptr));
-  // bhat = b_e - D_eo T_oo^-1 b_o and |bhat|
+  CU(cudaStreamSynchronize(ctx->stream));
+  // smallest cyclic run of timeslices t0 .. t0 + k - 1 holding every nonzero of b_o
+  int t0 = 0, k = T;
+  {
+    int nz = 0;
+    for (int t = 0; t < T; t++) nz += tsf[t] != 0;
+    if (nz == 0) k = 0;
+    else if (nz < T) {
+      int best = T;
+      for (int t = 0; t < T; t++) {          // a run ends where the next zero gap begins
+        if (!tsf[t] || tsf[(t + T - 1) % T]) continue;
+        int last = t, l = 0;
+        for (int d = 0; d < T; d++) if (tsf[(t + d) % T]) last = d;
+        l = last + 1;
+        if (l < best) { best = l; t0 = t; }
+      }
+      k = best;
+    }
+  }
+  // bhat = b_e - D_eo T_oo^-1 b_o and |bhat|.  With b_o supported on k + 4 < T
+  // timeslices (the sources of one source timeslice), T_oo^-1 b_o is formed on those
+  // k and zeroed on the two on either side, and the hop changes b_e only on the k + 2
+  // timeslices next to them: the rest of bhat is b_e.
   {
     HopOp a;
     a.p_out = 1; a.hop = 0; a.own = 1; a.kout = 3;
-    TRY(launch_hop(ctx, a, B.b_o, &B.b_o, B.t64o));
     HopOp b;
     b.p_out = 0; b.own = 1; b.kout = 0; b.s = -1.0;
-    TRY(launch_hop(ctx, b, B.t64o, &B.b_e, B.bh));
+    const size_t fb = field_bytes_per_rhs(DLMA_FP64, Vh) * nrhs;
+    if (ts_blocks && k + 4 < T) {
+      CU(cudaMemcpyAsync(B.bh.data, B.b_e.data, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (k > 0) {
+        // zero T_oo^-1 b_o on t0 - 2 .. t0 + k + 1: 12 nrhs rows of double2 per field
+        for (int d = -2; d < k + 2; d++) {
+          const int t = ((t0 + d) % T + T) % T;
+          CU(cudaMemset2DAsync((char*)B.t64o.data + (size_t)t * hsl * 16, (size_t)Vh * 16, 0, (size_t)hsl * 16,
+                               (size_t)12 * nrhs, ctx->stream));
+        }
+        a.site0 = t0 * hsl;
+        a.nsites = k * hsl;
+        TRY(launch_hop(ctx, a, B.b_o, &B.b_o, B.t64o));
+        b.site0 = ((t0 - 1 + T) % T) * hsl;
+        b.nsites = (k + 2) * hsl;
+        TRY(launch_hop(ctx, b, B.t64o, &B.b_e, B.bh));
+      }
+    } else {
+      TRY(launch_hop(ctx, a, B.b_o, &B.b_o, B.t64o));
+      TRY(launch_hop(ctx, b, B.t64o, &B.b_e, B.bh));
+    }
   }
   k_convert<DLMA_FP64, DLMA_FP64><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.bh.data, nullptr, B.t64.data, nullptr,
                                                               nullptr, 0, nullptr, B.part);
