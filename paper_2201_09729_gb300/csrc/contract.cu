@@ -804,7 +804,14 @@ static int pipeline_batch(dlma_ctx* ctx, int J, int granule) {
                          field_bytes_per_rhs(DLMA_FP32, ctx->g.Vh) * 8;
   size_t freeb = 0, totb = 0;
   cudaMemGetInfo(&freeb, &totb);
-  const size_t budget = ctx->memcap ? ctx->memcap : (size_t)(0.8 * (double)freeb);
+  // the work buffers this pipeline reuses (sources, solutions, the solver's fields)
+  // count as available: a repeated call must not size its batches by the memory its
+  // own previous call still holds
+  size_t held = 0;
+  for (int s : {WS_SRC, WS_SOL, WS_SOLVE_B, WS_SOLVE_X64, WS_SOLVE_R64, WS_SOLVE_BH, WS_SOLVE_TMP64, WS_CG_X, WS_CG_R,
+                WS_CG_P, WS_CG_PLO, WS_CG_Q, WS_CG_Z, WS_CG_TMP, WS_CG_RHS, WS_BI_S, WS_BI_R0, WS_RETRY_B, WS_RETRY_X})
+    held += ctx->wb[s].bytes;
+  const size_t budget = ctx->memcap ? ctx->memcap : (size_t)(0.8 * (double)(freeb + held));
   int nb = (int)std::max<size_t>((size_t)granule, std::min<size_t>((size_t)J, budget / per_rhs));
   return std::min(nb, J);
 }
