@@ -103,9 +103,6 @@ struct dlma_ctx {
   // in double-float (dfloat.cuh) for tol >= 1e-11; DLMA_DF_EIGS=0 at context
   // creation keeps FP64 arithmetic
   int df_eigs = 1;
-  // solves run as one persistent CUDA graph per batch (DLMA_SOLVE_GRAPH=0 at
-  // context creation launches the same passes from the host)
-  int solve_graph = 1;
   // solve batch size per precision, chosen by autotune_batch (valid up to batch_tuned_nb)
   int batch_rhs[3] = {0, 0, 0}, batch_tuned_nb[3] = {0, 0, 0}, batch_tuned[3] = {0, 0, 0};
 

@@ -420,7 +420,6 @@ extern "C" dlma_status dlma_create(const dlma_lattice* lat, int device, void* cu
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->err[0] = 0;
   if (const char* e = getenv("DLMA_DF_EIGS")) ctx->df_eigs = atoi(e) != 0;
-  if (const char* e = getenv("DLMA_SOLVE_GRAPH")) ctx->solve_graph = atoi(e) != 0;
   if (!ctx->stream) {
     // the legacy default stream cannot be captured into graphs: use a blocking
     // stream of our own (ordered with the legacy default stream)
