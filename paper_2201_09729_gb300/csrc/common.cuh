@@ -291,6 +291,10 @@ dlma_status solve_fields(dlma_ctx* ctx, const double* b_dev, double* x_dev, int 
 // V^dag psi on the tensor cores, FP64-accurate (split-precision digits): coeff[j][Tsel][4][N]
 dlma_status project_tc(dlma_ctx* ctx, const double2* VT, int N, int Tsel, const double* psi, size_t stride_sites,
                        int site_t0, int nrhs, double2* coeff);
+// sum over kappa of conj(B_k) A_r per timeslice on the tensor cores (tcproj.cu):
+// omode 1 writes out[t][k][r], omode 2 out[t][r][k]
+dlma_status tc_block_product(dlma_ctx* ctx, int omode, const double2* a_src, size_t a_st, size_t a_sr, size_t a_sk,
+                             int R, const double2* b_src, int b_conj, int N, int K, int T, double2* out);
 
 // per-context event timer helper
 struct EvTimer {

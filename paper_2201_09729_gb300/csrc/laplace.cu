@@ -23,7 +23,9 @@
 // matrix stays well conditioned) is formed in FP64.  Stops when every wanted
 // pair has ||A x - theta x|| <= tol max(theta, 1).  For tol >= 1e-11 the FP64
 // blocks' Gram matrices and rotations compute in double-float (~46 bits,
-// dfloat.cuh) on the FP32 units; the matvec and the small problems stay FP64.
+// dfloat.cuh) on the FP32 units or, for large blocks, with the split-digit
+// products of tcproj.cu on the tensor cores; the matvec and the small problems
+// stay FP64.
 //
 // Block layout (row-major per timeslice): element (t, row r = 3 site + colour,
 // column j) of a batch of Tn timeslices at (t * 3 Vs + r) * m + j, so a warp
@@ -462,6 +464,7 @@ struct Eig {
   dlma_ctx* ctx;
   int t0, Tn, N, m, n, nsplit, degree;
   int df = 0;   // phase B: Gram matrices and rotations in double-float (tol >= 1e-11)
+  int tc = 0;   // phase B: Gram matrices and rotations on the tensor cores (tcproj.cu)
   size_t blk;                    // m * Tn * n complex entries per block
   Cx<float> *F0, *F1, *F2, *F3;  // FP32 blocks
   Cx<double> *D0, *D1, *D2;      // FP64 blocks
@@ -518,6 +521,9 @@ template <class R> static dlma_status gram(Eig& E, const Cx<R>* X, const Cx<R>* 
   phase(E, kPhOrtho);
   const dim3 grid(tiles, E.nsplit, E.Tn);
   if constexpr (sizeof(R) == 8) {
+    if (E.tc)   // G[t][i][j] = sum_k conj(X[k][i]) Y[k][j]: rows = columns of Y, modes = columns of X
+      return tc_block_product(ctx, 1, (const double2*)Y, (size_t)E.n * E.m, 1, (size_t)E.m, E.m,
+                              (const double2*)X, 0, E.m, E.n, E.Tn, out);
     if (E.df) k_gram<R, df><<<grid, 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, herm, E.part);
     else k_gram<R, R><<<grid, 256, 0, ctx->stream>>>(X, Y, E.n, E.m, E.nsplit, herm, E.part);
   } else {
@@ -535,6 +541,9 @@ template <class R> static dlma_status rotate(Eig& E, const Cx<R>* X, Cx<R>* Z) {
   phase(E, kPhOrtho);
   const dim3 grid((E.n + RT - 1) / RT, (E.m + RT - 1) / RT, E.Tn);
   if constexpr (sizeof(R) == 8) {
+    if (E.tc)   // Z[t][k][j] = sum_l X[k][l] C[l][j]: rows = rows of X, modes = conj of the columns of C
+      return tc_block_product(ctx, 2, (const double2*)X, (size_t)E.n * E.m, (size_t)E.m, 1, E.n, E.C, 1, E.m, E.m,
+                              E.Tn, (double2*)Z);
     if (E.df) k_rotate<R, df><<<grid, 256, 0, ctx->stream>>>(X, E.C, E.n, E.m, Z);
     else k_rotate<R, R><<<grid, 256, 0, ctx->stream>>>(X, E.C, E.n, E.m, Z);
   } else {
@@ -784,6 +793,12 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   // The FP64 blocks' Gram matrices and rotations run in double-float on the FP32
   // units when the tolerance leaves room for its ~2^-46 rounding.
   E.df = ctx->df_eigs && tol >= 1e-11;
+  // large blocks take the tensor cores (32^3 x 64, N = 96: orthogonalisation 5.4 ->
+  // 4.4 s); small ones stay in double-float, where the tensor-core launches do not
+  // fill the GPU (16^3 x 32, N = 32: 65 against 70 ms).  DLMA_EIGS_TC=1 / 0 forces
+  // either.
+  E.tc = E.df && (size_t)E.n * E.m * E.Tn >= ((size_t)1 << 27);
+  if (const char* e = getenv("DLMA_EIGS_TC")) E.tc = E.df && atoi(e) == 1;
   Cx<double> *X64 = E.D0, *W64 = E.D1, *Y64 = E.D2;
   // phase A's last Ritz pairs were not fetched, or hold refilled (random) columns
   const bool rr_first = E.refilled || it >= maxA;

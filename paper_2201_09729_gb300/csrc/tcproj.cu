@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(128) k_slice_psi(const double2* __restrict__ p
 // (re coefficient: re v, im v) and row 32 + kk (im coefficient: -im v, re v).
 // VT is [t][kappa][k] (mode fastest).
 __global__ void __launch_bounds__(128) k_slice_modes(const double2* __restrict__ VT, int N, int K, int Tg, int t0,
-                                                     int q0, int Qg, int MB, uint8_t* Bs, int* eB, int* eBmax) {
+                                                     int q0, int Qg, int MB, uint8_t* Bs, int* eB, int* eBmax,
+                                                     int conj_in = 0) {
   const long wg = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const long total = (long)Tg * MB * Qg * 32;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(128) k_slice_modes(const double2* __restrict__
     double2 v = make_double2(0, 0);
     if (k < N && kappa < K) v = VT[((size_t)(t0 + tl) * K + kappa) * N + k];
     x[2 * u] = v.x;
-    x[2 * u + 1] = v.y;
+    x[2 * u + 1] = conj_in ? -v.y : v.y;
   }
   int ex = kExpZero;
 #pragma unroll
@@ -212,6 +213,54 @@ __global__ void __launch_bounds__(128) k_slice_modes(const double2* __restrict__
   }
 }
 
+// A digits of a generic complex source: row r of timeslice t, element kappa at
+// src[t st + r sr + kappa sk] (one warp per (t, row, chunk q); the lanes as in
+// k_slice_psi).  Rows r >= R and kappa >= K are zero.
+__global__ void __launch_bounds__(128) k_slice_agen(const double2* __restrict__ src, size_t st, size_t sr, size_t sk,
+                                                    int Tg, int R, int K, int q0, int Qg, int RT, uint8_t* As, int* eA,
+                                                    int* eAmax) {
+  const long wg = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long total = (long)Tg * RT * TM * Qg;
+  if (wg >= total) return;
+  const int ql = (int)(wg % Qg);
+  const long rest = wg / Qg;
+  const int row = (int)(rest % (RT * TM));
+  const int tl = (int)(rest / (RT * TM));
+  const int q = q0 + ql;
+  const int b = lane / 4, kc = lane % 4;
+  const int rt = row / TM, rr = row % TM;
+  double x[8];
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const int kappa = q * CK + 4 * lane + u;
+    double2 v = make_double2(0, 0);
+    if (row < R && kappa < K) v = src[(size_t)tl * st + (size_t)row * sr + (size_t)kappa * sk];
+    x[2 * u] = v.x;
+    x[2 * u + 1] = v.y;
+  }
+  int ex = kExpZero;
+#pragma unroll
+  for (int u = 0; u < 8; u++) ex = max(ex, exp_above(x[u]));
+  const int e = warp_max_int(ex);
+  if (lane == 0) {
+    eA[((size_t)(tl * RT + rt) * Qg + ql) * TM + rr] = e;
+    atomicMax(eAmax + (size_t)tl * RT * TM + row, e);
+  }
+  float d[8][S];
+#pragma unroll
+  for (int u = 0; u < 8; u++) digits(x[u], e, d[u]);
+  const size_t tile0 = (((size_t)(tl * RT + rt) * Qg + ql) * NBK + b) * S;
+  const size_t off = (size_t)(rr / 8) * SBO + kc * LBO + (rr % 8) * 16;
+#pragma unroll
+  for (int s = 0; s < S; s++) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) v[u] = d[u][s];
+    *(uint4*)(As + (tile0 + s) * A_TILE + off) = pack8(v);
+  }
+}
+
 __global__ void k_fill_int(int* p, size_t n, int v) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) p[e] = v;
@@ -224,7 +273,7 @@ __global__ void __launch_bounds__(320, 1) k_proj_mma(const uint8_t* __restrict__
                                                      const int* __restrict__ eA, const int* __restrict__ eB,
                                                      const int* __restrict__ eAmax, const int* __restrict__ eBmax,
                                                      int Qg, int RT, int MB, int R, int N, int Tsel, int t0,
-                                                     int accumulate, double* coeff, int* err) {
+                                                     int accumulate, double* coeff, int* err, int omode = 0) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[2], empty[2], accf, acce, drain;
   __shared__ uint32_t tbase;
@@ -368,7 +417,11 @@ __global__ void __launch_bounds__(320, 1) k_proj_mma(const uint8_t* __restrict__
       for (int n = 0; n < 32; n++) {
         const int k = mb * 32 + n;
         if (k >= N) break;
-        double* o = coeff + 2 * ((((size_t)j * Tsel + t0 + tl) * 4 + alpha) * N + k) + half;
+        // omode 0: coeff[j][t][alpha][k]; 1: out[t][k][row]; 2: out[t][row][k]
+        const size_t idx = omode == 0 ? (((size_t)j * Tsel + t0 + tl) * 4 + alpha) * N + k
+                           : omode == 1 ? ((size_t)(t0 + tl) * N + k) * R + grow
+                                        : ((size_t)(t0 + tl) * R + grow) * N + k;
+        double* o = coeff + 2 * idx + half;
         const double v = ldexp((double)hi[n] + (double)lo[n], ra + rb[n]);
         *o = accumulate ? *o + v : v;
       }
@@ -433,5 +486,57 @@ dlma_status project_tc(dlma_ctx* ctx, const double2* VT, int N, int Tsel, const 
   CU(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   if (h) return set_err(ctx, DLMA_ERR_CUDA, "tensor-core projection: a pipeline wait timed out");
+  return DLMA_OK;
+}
+
+// Block products of the eigensolver's FP64 phase on the tensor cores, with the same
+// FP64-accurate digit scheme.  For every timeslice t:
+//   out[t] (omode 1: [N][R], omode 2: [R][N]) holds sum_kappa conj(B_k(kappa)) A_r(kappa)
+// with A_r(kappa) = a_src[t a_st + r a_sr + kappa a_sk] (R rows, K long) and
+// B_k(kappa) = b_src[(t K + kappa) N + k] (conjugated first when b_conj).
+dlma_status tc_block_product(dlma_ctx* ctx, int omode, const double2* a_src, size_t a_st, size_t a_sr, size_t a_sk,
+                             int R, const double2* b_src, int b_conj, int N, int K, int T, double2* out) {
+  if (omode != 1 && omode != 2) return set_err(ctx, DLMA_ERR_INVALID_ARG, "tc_block_product mode");
+  const int Q = (K + CK - 1) / CK;
+  const int RT = (R + TM - 1) / TM, MB = (N + 31) / 32;
+  const size_t per_chunk = (size_t)T * NBK * S * ((size_t)RT * A_TILE + (size_t)MB * B_TILE);
+  size_t budget = (size_t)4 << 30;
+  if (ctx->memcap) budget = std::min(budget, (size_t)ctx->memcap / 4);
+  const int Qg = (int)std::max<size_t>(1, std::min<size_t>((size_t)Q, budget / per_chunk));
+  uint8_t *As, *Bs;
+  int *eA, *eB;
+  TRY(workT(ctx, WS_TC_A, (size_t)T * RT * Qg * NBK * S * A_TILE, &As));
+  TRY(workT(ctx, WS_TC_B, (size_t)T * MB * Qg * NBK * S * B_TILE, &Bs));
+  TRY(workT(ctx, WS_TC_E, (size_t)T * (Qg + 1) * (RT * TM + MB * TN), &eA));
+  eB = eA + (size_t)T * Qg * RT * TM;
+  int* eAmax = eB + (size_t)T * Qg * MB * TN;
+  int* eBmax = eAmax + (size_t)T * RT * TM;
+  const size_t nref = (size_t)T * (RT * TM + MB * TN);
+  int* err = ctx->flag + 8;
+  CU(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  static bool attr_set[64] = {false};
+  if (ctx->device >= 0 && ctx->device < 64 && !attr_set[ctx->device]) {
+    CU(cudaFuncSetAttribute(k_proj_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr_set[ctx->device] = true;
+  }
+  for (int q0 = 0; q0 < Q; q0 += Qg) {
+    const int qn = std::min(Qg, Q - q0);
+    const long wa = (long)T * RT * TM * qn, wb = (long)T * MB * qn * 32;
+    k_fill_int<<<(unsigned)((nref + 255) / 256), 256, 0, ctx->stream>>>(eAmax, nref, kExpZero);
+    CHECK_LAUNCH();
+    k_slice_agen<<<(unsigned)((wa + 3) / 4), 128, 0, ctx->stream>>>(a_src, a_st, a_sr, a_sk, T, R, K, q0, qn, RT, As,
+                                                                    eA, eAmax);
+    CHECK_LAUNCH();
+    k_slice_modes<<<(unsigned)((wb + 3) / 4), 128, 0, ctx->stream>>>(b_src, N, K, T, 0, q0, qn, MB, Bs, eB, eBmax,
+                                                                     b_conj);
+    CHECK_LAUNCH();
+    k_proj_mma<<<dim3(RT, MB, T), 320, SMEM_BYTES, ctx->stream>>>(As, Bs, eA, eB, eAmax, eBmax, qn, RT, MB, R, N, T,
+                                                                 0, q0 > 0 ? 1 : 0, (double*)out, err, omode);
+    CHECK_LAUNCH();
+  }
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (h) return set_err(ctx, DLMA_ERR_CUDA, "tensor-core block product: a pipeline wait timed out");
   return DLMA_OK;
 }

@@ -25,8 +25,9 @@ def test_eigs_df_phase_against_fp64(dl, monkeypatch):
     L, T, N = 8, 4, 16
     U = synth.gauge_field(L, T, 0.2, 613)
     res = {}
-    for flag in ("1", "0"):
-        monkeypatch.setenv("DLMA_DF_EIGS", flag)
+    for flag in ("1", "tc", "0"):
+        monkeypatch.setenv("DLMA_DF_EIGS", "0" if flag == "0" else "1")
+        monkeypatch.setenv("DLMA_EIGS_TC", "1" if flag == "tc" else "0")
         ctx = dl.Context(L, T, 0, 0)
         ctx.dlma_set_gauge(U)
         lam, V = ctx.dlma_laplacian_eigs(-1, N, 1e-10)
@@ -43,3 +44,4 @@ def test_eigs_df_phase_against_fp64(dl, monkeypatch):
             assert np.abs(gram - np.eye(N)).max() < 1e-11
         ctx.close()
     assert np.abs(res["1"] - res["0"]).max() <= 1e-10 * np.abs(res["0"]).max()
+    assert np.abs(res["tc"] - res["0"]).max() <= 1e-10 * np.abs(res["0"]).max()
