@@ -96,10 +96,12 @@ template <class R, class A> __device__ __forceinline__ Cx<R> to_s(Cx<A> v) { ret
 // out = alpha_t (A in) + beta_t in + gamma_t prev + alpha_t s[t][j] rin,  A = 6 - hopping = -lap
 // (in == nullptr: the stencil and beta terms vanish; prev / rin may be nullptr).
 // One thread per (site, NC adjacent columns): the six links of the site are loaded
-// (and, in FP32, rebuilt from 12 reals) once for NC columns.  The block is
+// (and, in FP32, rebuilt from 12 reals) once for NC columns.  The FP32 form is
+// compiled for three blocks per SM (80 registers, a few spilled words: matvec of
+// 16^3 x 32, N = 32, 61 -> 56 ms against two blocks), FP64 for two.  The block is
 // [t][site][colour][m] with m even, so a pair of FP32 columns is 16-byte aligned.
 template <class R, class A, int NC>
-__global__ void __launch_bounds__(256) k_lap(Geom g, int t0, int Tn, int m, const typename LinkT<R>::T* __restrict__ U,
+__global__ void __launch_bounds__(256, sizeof(A) == 4 ? 3 : 2) k_lap(Geom g, int t0, int Tn, int m, const typename LinkT<R>::T* __restrict__ U,
                                              const Cx<R>* __restrict__ in, const Cx<R>* __restrict__ prev,
                                              const Cx<float>* __restrict__ rin, const double* __restrict__ scol,
                                              Cx<R>* __restrict__ out, const double* __restrict__ coef) {
