@@ -593,24 +593,41 @@ __global__ void __launch_bounds__(BX) k_bi_p(int Vh, int nrhs, const void* r, vo
   store_spinor<P>((char*)p + sb, nullptr, Vh, i, pv);
 }
 
-// partials of sum conj(a) b and |b|^2 per (rhs, block) for the rhs in mask
+// End of a BiCGStab reliable update in one pass over the updated rhs: r_l = r64 / s_j
+// (FP64 -> P); where the shadow residual restarts (rmask) r0 = p = r_l; partials of
+// (r0, r_l) and |r_l|^2 for k_bi_resume
 template <int P>
-__global__ void __launch_bounds__(BX) k_dot_norm(int Vh, int nrhs, const void* a, const void* b, const int* mask,
-                                                 double2* cpart, double* npart) {
+__global__ void __launch_bounds__(BX) k_bi_restore(int Vh, int nrhs, const double2* r64, const double* f, void* rl,
+                                                   void* r0, void* pl, const int* upd, const int* rmask,
+                                                   double2* cpart, double* npart) {
   typedef typename PT<P>::R R;
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y;
-  const bool on = mask[j] != 0;
+  const bool on = upd[j] != 0;
   double dr = 0, di = 0, nn = 0;
   if (i < Vh && on) {
-    const size_t sb = field_units_per_rhs(P, Vh) * 16 * j;
-    const Spinor<R> av = load_spinor<P>((const char*)a + sb, nullptr, Vh, i);
-    const Spinor<R> bv = load_spinor<P>((const char*)b + sb, nullptr, Vh, i);
+    const size_t so = field_units_per_rhs(P, Vh) * 16 * j;
+    const Spinor<double> v = load_spinor<DLMA_FP64>((const char*)r64 + (size_t)192 * Vh * j, nullptr, Vh, i);
+    const double ff = f[j] > 0 ? 1.0 / f[j] : 0.0;
+    Spinor<R> o;
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) o.c[s][c] = cx<R>((R)(ff * v.c[s][c].re), (R)(ff * v.c[s][c].im));
+    store_spinor<P>((char*)rl + so, nullptr, Vh, i, o);
+    Spinor<R> a;
+    if (rmask[j]) {
+      store_spinor<P>((char*)r0 + so, nullptr, Vh, i, o);
+      store_spinor<P>((char*)pl + so, nullptr, Vh, i, o);
+      a = o;
+    } else {
+      a = load_spinor<P>((const char*)r0 + so, nullptr, Vh, i);
+    }
 #pragma unroll
     for (int s = 0; s < 4; s++)
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        const Cx<R> x = av.c[s][c], y = bv.c[s][c];
+        const Cx<R> x = a.c[s][c], y = o.c[s][c];
         dr += (double)x.re * y.re + (double)x.im * y.im;
         di += (double)x.re * y.im - (double)x.im * y.re;
         nn += (double)y.re * y.re + (double)y.im * y.im;
@@ -1239,18 +1256,10 @@ static dlma_status bicg_update(dlma_ctx* ctx, SolveBufs& B, int nrhs, double tol
   k_ru_check<<<nb1, 128, 0, ctx->stream>>>(nrhs, B.sc, tol_target);
   CHECK_LAUNCH();
   const int* upd = B.sc.upd;
-  k_convert<DLMA_FP64, P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.r64.data, nullptr, B.rl.data, nullptr, B.sc.scale,
-                                                      1, upd, nullptr);
-  CHECK_LAUNCH();
   k_bi_restart_mask<<<nb1, 128, 0, ctx->stream>>>(nrhs, B.sc, B.bs, first ? 1 : 0, B.rmask);
   CHECK_LAUNCH();
-  k_convert<P, P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, nullptr, B.r0.data, nullptr, nullptr, 0, B.rmask,
-                                              nullptr);
-  CHECK_LAUNCH();
-  k_convert<P, P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.rl.data, nullptr, B.pl.data, nullptr, nullptr, 0, B.rmask,
-                                              nullptr);
-  CHECK_LAUNCH();
-  k_dot_norm<P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, B.r0.data, B.rl.data, upd, B.cpart2, B.part2);
+  k_bi_restore<P><<<gv, BX, 0, ctx->stream>>>(Vh, nrhs, (const double2*)B.r64.data, B.sc.scale, B.rl.data, B.r0.data,
+                                               B.pl.data, upd, B.rmask, B.cpart2, B.part2);
   CHECK_LAUNCH();
   k_bi_resume<<<(nrhs + 3) / 4, 128, 0, ctx->stream>>>(B.cpart2, B.part2, gv.x, nrhs, B.sc, B.bs, delta2);
   CHECK_LAUNCH();
