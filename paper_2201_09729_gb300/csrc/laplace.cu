@@ -568,7 +568,7 @@ template <class T> static dlma_status small_rr(Eig& E) {
   if (use_smem) CU(cudaFuncSetAttribute(k_small_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   CU(cudaMemsetAsync(E.dropped, 0, sizeof(int), ctx->stream));
   const int chol = 1;
-  k_small_rr<T><<<E.Tn, 256, use_smem ? sm : 0, ctx->stream>>>(E.G, E.H, E.m, E.C, E.theta, (Cx<T>*)E.gwork,
+  k_small_rr<T><<<E.Tn, 1024, use_smem ? sm : 0, ctx->stream>>>(E.G, E.H, E.m, E.C, E.theta, (Cx<T>*)E.gwork,
                                                                use_smem, E.dropped, E.drop_rel, chol);
   CHECK_LAUNCH();
   return DLMA_OK;

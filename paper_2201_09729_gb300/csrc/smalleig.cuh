@@ -122,7 +122,7 @@ __device__ int jacobi(Cx<T>* A, Cx<T>* V, int m, int ld, T* rc, T* rs, Cx<T>* re
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_small_rr(const double2* Gall, const double2* Hall, int m, double2* Call,
+__global__ void __launch_bounds__(1024) k_small_rr(const double2* Gall, const double2* Hall, int m, double2* Call,
                                                   double* theta_all, Cx<T>* gwork, int use_smem, int* dropped,
                                                   double drop_rel, int chol = 0) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
