@@ -561,15 +561,14 @@ template <class R> static dlma_status rotate(Eig& E, const Cx<R>* X, Cx<R>* Z) {
 // phase-A block can have) falls back to the Jacobi route inside the kernel.
 template <class T> static dlma_status small_rr(Eig& E) {
   dlma_ctx* ctx = E.ctx;
-  const size_t sm = (size_t)3 * E.m * (E.m + 1) * sizeof(Cx<T>);   // three m x (m + 1) work matrices
-  // the kernel also holds ~11 KB of static shared memory: always raise the dynamic limit
-  const int use_smem = sm <= 200 * 1024;
+  size_t sm = 0;
+  const int place = small_rr_place<T>(E.m, &sm);
   phase(E, kPhOrtho);
-  if (use_smem) CU(cudaFuncSetAttribute(k_small_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  if (sm) CU(cudaFuncSetAttribute(k_small_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   CU(cudaMemsetAsync(E.dropped, 0, sizeof(int), ctx->stream));
   const int chol = 1;
-  k_small_rr<T><<<E.Tn, 1024, use_smem ? sm : 0, ctx->stream>>>(E.G, E.H, E.m, E.C, E.theta, (Cx<T>*)E.gwork,
-                                                               use_smem, E.dropped, E.drop_rel, chol);
+  k_small_rr<T><<<E.Tn, 1024, sm, ctx->stream>>>(E.G, E.H, E.m, E.C, E.theta, (Cx<T>*)E.gwork, place, E.dropped,
+                                                 E.drop_rel, chol);
   CHECK_LAUNCH();
   return DLMA_OK;
 }
@@ -795,11 +794,12 @@ static dlma_status eig_batch(dlma_ctx* ctx, int t0, int Tn, int N, double tol, d
   // The FP64 blocks' Gram matrices and rotations run in double-float on the FP32
   // units when the tolerance leaves room for its ~2^-46 rounding.
   E.df = ctx->df_eigs && tol >= 1e-11;
-  // large blocks take the tensor cores (32^3 x 64, N = 96: orthogonalisation 5.4 ->
-  // 4.4 s); small ones stay in double-float, where the tensor-core launches do not
-  // fill the GPU (16^3 x 32, N = 32: 65 against 70 ms).  DLMA_EIGS_TC=1 / 0 forces
-  // either.
-  E.tc = E.df && (size_t)E.n * E.m * E.Tn >= ((size_t)1 << 27);
+  // products of many multiply-adds (n m^2 per timeslice) take the tensor cores
+  // (16^3 x 32: orthogonalisation 250 -> 200 ms at N = 64, 617 -> 533 ms at N = 128;
+  // 32^3 x 64, N = 96: 5.4 -> 4.4 s); small ones stay in double-float, where the
+  // tensor-core launches do not fill the GPU (16^3 x 32, N = 32: 65 against 70 ms).
+  // DLMA_EIGS_TC=1 / 0 forces either.
+  E.tc = E.df && (double)E.n * E.m * E.m * E.Tn >= 4.0e9;
   if (const char* e = getenv("DLMA_EIGS_TC")) E.tc = E.df && atoi(e) == 1;
   Cx<double> *X64 = E.D0, *W64 = E.D1, *Y64 = E.D2;
   // phase A's last Ritz pairs were not fetched, or hold refilled (random) columns

@@ -169,14 +169,13 @@ static dlma_status rayleigh_ritz(DiracEig& E, double2* X, double2* AX, int m) {
   dlma_ctx* ctx = E.ctx;
   TRY(gram(E, X, X, m, m, E.G));
   TRY(gram(E, X, AX, m, m, E.H));
-  const size_t sm = (size_t)3 * m * (m + 1) * sizeof(Cx<double>);
-  const int use_smem = sm <= 200 * 1024;
-  if (use_smem)
+  size_t sm = 0;
+  const int place = lma_small::small_rr_place<double>(m, &sm);
+  if (sm)
     CU(cudaFuncSetAttribute(lma_small::k_small_rr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   CU(cudaMemsetAsync(E.dropped, 0, sizeof(int), ctx->stream));
-  lma_small::k_small_rr<double><<<1, 256, use_smem ? sm : 0, ctx->stream>>>(E.G, E.H, m, E.C, E.theta,
-                                                                            (Cx<double>*)E.gwork, use_smem,
-                                                                            E.dropped, 1e-24);
+  lma_small::k_small_rr<double><<<1, 256, sm, ctx->stream>>>(E.G, E.H, m, E.C, E.theta, (Cx<double>*)E.gwork, place,
+                                                             E.dropped, 1e-24);
   CHECK_LAUNCH();
   TRY(rotate(E, X, E.C, m, m, E.Y));
   CU(cudaMemcpyAsync(X, E.Y, sizeof(double2) * E.n * m, cudaMemcpyDeviceToDevice, ctx->stream));
