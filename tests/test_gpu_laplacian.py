@@ -110,6 +110,28 @@ def test_eigs_block_above_256_columns(dl):
         assert np.abs(gram - np.eye(N)).max() < 1e-11
 
 
+@pytest.mark.parametrize("N", [64, 100])
+def test_eigs_small_problem_placements(dl, N):
+    # the small Rayleigh-Ritz problems keep the packed matrix and then S in shared
+    # memory while they fit: m = 128 puts the FP64 phase's S in global memory, m = 164
+    # the FP32 phase's S and the whole FP64 problem (m = 264, both phases in global
+    # memory, is the test above)
+    L, T = 8, 2
+    U = synth.gauge_field(L, T, 0.2, 233 + N)
+    ctx = dl.Context(L, T, 0, 0)
+    ctx.dlma_set_gauge(U)
+    lam, V = ctx.dlma_laplacian_eigs(-1, N, 1e-10)
+    for t in range(T):
+        Ut = lap.timeslice_links(U, L, t)
+        w, _ = lap.lap_modes(Ut, L, N)
+        assert np.all(np.abs(lam[t] - w) <= 1e-9 * np.maximum(np.abs(w), 1.0))
+        for k in (0, N // 3, N - 1):
+            r = -lap.lap_apply(Ut, L, V[t, k]) - lam[t, k] * V[t, k]
+            assert np.linalg.norm(r) <= 1e-9 * max(1.0, lam[t, k])
+        gram = np.einsum("kmc,lmc->kl", np.conj(V[t]), V[t])
+        assert np.abs(gram - np.eye(N)).max() < 1e-11
+
+
 def test_eigs_tight_tolerance_small_lattice(dl):
     # 6^3 x 4 with N = 4 to 1e-12: the filtered columns of the FP64 phase are
     # rescaled to unit size, so the Gram matrix does not limit the accuracy
