@@ -162,9 +162,9 @@ dlma_status dlma_apply_schur_noalloc(dlma_ctx* ctx, const double* in, double* ou
  * DLMA_FP16S run the Krylov iteration in that precision (FP16: storage, FP32
  * arithmetic) with FP64 reliable updates: when a right-hand side's iterated
  * residual has dropped by a fixed factor since its last update, its solution
- * is folded into FP64 and its residual recomputed in FP64.  Each right-hand
- * side stops when its FP64 true residual
- * ||b - D x|| / ||b|| <= tol and is retired from the batch.  `info` (may be
+ * is folded into FP64 and its residual recomputed in FP64 (for BiCGStab's
+ * last update see dlma_set_solver).  Each right-hand side stops when its
+ * FP64 true residual ||b - D x|| / ||b|| <= tol and is retired from the batch.  `info` (may be
  * NULL) receives nrhs records.  A zero source gives x = 0.
  * Errors: STATE, INVALID_ARG (tol <= 0, nrhs < 1), NOT_CONVERGED, NONFINITE,
  * OOM, CUDA. */
@@ -175,8 +175,13 @@ dlma_status dlma_solve(dlma_ctx* ctx, const double* b, double* x, int nrhs, doub
  * (the FP64 and FP16S inner solves always run CGNE).  DLMA_SOLVER_BICGSTAB
  * (the default) iterates BiCGStab on the Schur system Dhat x_e = bhat with
  * FP32 vectors and the same FP64 reliable updates (residual replacement when
- * |r| has dropped by 1e-3 since the last update; restart of the shadow
- * residual after a breakdown or a stagnating update): two operator
+ * |r| has dropped by 3e-4 since the last update, DLMA_BICG_DELTA in the
+ * environment overriding the factor; restart of the shadow residual after a
+ * breakdown or a stagnating update).  The iteration aims at tol / 2; once a
+ * right-hand side's FP64 residual is below 1e-3 (tol / 2) / 1.2e-7 times |b|,
+ * its next update subtracts the FP32 operator's image of the FP32 solution
+ * increment from that residual instead of applying the FP64 operator: the
+ * FP32 rounding of the small product stays below 1e-3 (tol / 2) |b|.  Two operator
  * applications per iteration and about half as many as CGNE needs on these
  * systems.  Right-hand sides it leaves above the tolerance are solved again
  * with CGNE in the same call; their info sums both iteration counts.
